@@ -1,0 +1,314 @@
+"""Benchmark of the thermal MRT lattice-Boltzmann hot path (arXiv:1809.08683)
+on GB300.
+
+Default workload: the batched sweep of 96 heated cavities (sides 192..1024
+from Ra log-uniform in [1e3, 1e8], eps in [0.1, 0.6], ideal or cubic EOS,
+FP32 deviation storage; 39.2M nodes, 11 GB of DFs), advanced together.  One
+bench step = `--chunk` time steps of every cavity (fused collide + stream
+launch and wall-pass launch per time step).  Metric: MLUPS, one lattice-node
+update of both f and g per node per time step.
+
+Lines printed (one JSON line per run, rank 0):
+  value     device-timed MLUPS over the timed region (CUDA events, inputs
+            resident in HBM; state 11 GB >> 129 MB L2, so no flush is needed)
+  e2e       same metric through the public API with host buffers: per bench
+            step, equilibrium initialisation from pinned host fields (H2D),
+            the chunk of time steps, and the macroscopic fields back (D2H)
+  roofline  the fused kernel's algorithmic bytes (18 DF reads + 18 DF writes
+            per node) over its CUDA-event duration, against the measured HBM
+            copy bandwidth
+  cpu_baseline  the FP64 CPU oracle on a bounded sample (rank 0, N = 1)
+`--impl reference` times that oracle alone (the reference arm).
+Multi-GPU: instances are independent, so each rank advances its own copy of
+the batch (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1809_08683_gb300 import workloads as W  # noqa: E402
+
+BYTES_PER_NODE = {0: 288, 1: 144}   # 18 DF reads + 18 DF writes, FP64 / FP32
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batched_sweep",
+                    choices=["batched_sweep", "cavity512", "cavity4096", "poiseuille"])
+    ap.add_argument("--precision", type=int, default=None, help="0 FP64, 1 FP32-deviation")
+    ap.add_argument("--chunk", type=int, default=None, help="time steps per bench step")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name, precision):
+    if name == "batched_sweep":
+        p = 1 if precision is None else precision
+        cfgs = W.batched_sweep(precision=p)
+        desc = {"workload": "batched_sweep_96_cavities", "instances": len(cfgs), "seed": 1809,
+                "sides": "192..1024 from Ra in [1e3,1e8]", "eos": "ideal|cubic(a=0.05,b=0.2)",
+                "precision": "fp32_dev" if p else "fp64"}
+        return cfgs, desc, 100
+    if name == "cavity512":
+        p = 1 if precision is None else precision
+        cfgs = [W.cavity(N=512, Ra=1e6, eps=0.6, precision=p)]
+        return cfgs, {"workload": "cavity_512x512_Ra1e6_eps0.6", "precision": "fp32_dev" if p else "fp64"}, 1000
+    if name == "cavity4096":
+        p = 1 if precision is None else precision
+        cfgs = [W.cavity(N=4096, Ra=1e8, eps=0.6, precision=p)]
+        return cfgs, {"workload": "cavity_4096x4096_Ra1e8_eps0.6", "precision": "fp32_dev" if p else "fp64"}, 20
+    p = 0 if precision is None else precision
+    cfgs = [W.poiseuille(nx=4, ny=128, precision=p)]
+    return cfgs, {"workload": "poiseuille_4x128_cubic", "precision": "fp32_dev" if p else "fp64"}, 1000
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 7 and parts[0].replace(".", "").isdigit():
+                    rows.append(parts)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[0]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(rows[0][1]), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_baseline(cfgs, budget_s=12.0):
+    """The FP64 CPU oracle, as it stands, on a bounded sample: the first
+    lattice of the workload, stepped until about budget_s seconds pass."""
+    import oracle
+    cores = os.cpu_count() or 1
+    oracle.build()
+    cfg = dict(cfgs[0])
+    o = oracle.Oracle(cfg, threads=cores)
+    nodes = cfg["nx"] * cfg["ny"]
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        o.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or steps >= 100000:
+            break
+    o.close()
+    return {"value": nodes * steps / el / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{cfg['nx']}x{cfg['ny']} lattice (first of the workload), {steps} steps, FP64, "
+                      f"{el:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cfgs, desc, _ = workload(args.workload, args.precision)
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    cfg = dict(cfgs[0])
+    o = oracle.Oracle(cfg, threads=cores)
+    nodes = cfg["nx"] * cfg["ny"]
+    per_step = max(1, int(2e6 // nodes))   # about 1-2 s of oracle work per bench step
+    for _ in range(args.warmup):
+        o.step(per_step)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(per_step)
+    el = time.perf_counter() - t0
+    v = nodes * per_step * args.steps / el / 1e6
+    sample = f"{cfg['nx']}x{cfg['ny']} lattice (first of the workload), {per_step} time steps per bench step, FP64"
+    print(json.dumps({
+        "impl": "reference", "metric": "MLUPS", "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": desc,
+        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+    from paper_1809_08683_gb300 import lbm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    lbm.build()
+    lbm.load()
+
+    cfgs, desc, chunk = workload(args.workload, args.precision)
+    chunk = args.chunk or chunk
+    stream = torch.cuda.Stream(device=dev)
+    lats = [lbm.Lattice(c, stream=stream, device=dev) for c in cfgs]
+    batch = lbm.Batch(lats, graph_steps=0)
+    nodes = sum(c["nx"] * c["ny"] for c in cfgs)
+    prec = int(cfgs[0].get("precision", 0))
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        batch.step_profiled(chunk)
+    barrier()
+
+    t_collide = t_wall = 0.0
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            a, b = batch.step_profiled(chunk)
+            t_collide += a
+            t_wall += b
+        ev1.record(stream)
+        ev1.synchronize()
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    steps_total = args.steps * chunk
+    value = nodes * steps_total * world / (ms * 1e-3) / 1e6
+    clocks = clk.summary()
+
+    # fused kernel against the HBM roofline
+    peak, peak_kind = read_peaks()
+    avg_collide_ms = t_collide / steps_total
+    alg_bytes = nodes * BYTES_PER_NODE[prec]
+    achieved = alg_bytes / (avg_collide_ms * 1e-3) / 1e9
+    n_collide_launches = 1
+    gpu_launches = args.steps * chunk * (n_collide_launches + 1)
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        host_in = []
+        for c in cfgs:
+            shp = (c["ny"], c["nx"])
+            fields = []
+            for v in (1.0, 0.0, 0.0, 1.0):
+                t = torch.full(shp, v, dtype=torch.float64).pin_memory()
+                fields.append(t.numpy())
+            host_in.append(fields)
+        host_out = [[torch.empty((c["ny"], c["nx"]), dtype=torch.float64).pin_memory().numpy()
+                     for _ in range(5)] for c in cfgs]
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            for lat, f in zip(lats, host_in):
+                lat.init_macros(*f)
+            batch.step(chunk)
+            for lat, o in zip(lats, host_out):
+                lat.check(lat.L.lbm_macros(lat.h, *(lbm._ptr(a) for a in o)))
+        barrier()
+        el = time.perf_counter() - t0
+        e2e = {"value": nodes * chunk * args.e2e_steps * world / el / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": nodes * 4 * 8, "d2h_bytes_per_step": nodes * 5 * 8}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(cfgs)
+
+    if rank == 0:
+        desc = dict(desc)
+        desc.update({"nodes": nodes, "time_steps_per_bench_step": chunk,
+                     "l2": "state larger than L2 (no flush)" if alg_bytes > 2 * 129e6 else "state may be L2-resident"})
+        out = {
+            "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec else "f64",
+            "data": "synthetic", "config": desc,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                         "kernel": "k_collide_stream", "alg_bytes_per_launch": alg_bytes,
+                         "avg_launch_ms": avg_collide_ms, "wall_pass_ms_per_step": t_wall / steps_total},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clocks,
+        }
+        print(json.dumps(out))
+    batch.close()
+    for lat in lats:
+        lat.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,169 @@
+/*
+ * C ABI of the GB300 (sm_103a) thermal MRT lattice-Boltzmann hot path:
+ * Huang, Wu & Adams, "Lattice Boltzmann model with self-tuning equation of
+ * state for coupled thermo-hydrodynamic flows", arXiv:1809.08683.
+ *
+ * One context = one D2Q9 lattice of nx * ny nodes (x fastest) carrying the
+ * density DF f_i (Sec. 2.1, Eqs. LBE.u) and the total-energy DF g_i
+ * (Sec. 2.2, Eqs. LBE.T), with the wall treatment of Sec. 3 on every
+ * non-periodic side.  Lattice units: c = dx = dt = 1, c_s^2 = 1/3.
+ *
+ * Conventions
+ *  - Every call returns an lbm_status; no exception or signal crosses the ABI.
+ *    On error, lbm_last_error() returns a per-thread message (never freed by
+ *    the caller).  A detected NaN/Inf (LBM_EUNSTABLE) is sticky until
+ *    lbm_set_eos(), lbm_init_macros() or lbm_set_state() re-initialises.
+ *  - Device memory: the caller passes one device buffer of
+ *    lbm_workspace_bytes() bytes (256-byte aligned, owned by the caller,
+ *    kept alive until lbm_destroy()); passing NULL makes the library
+ *    allocate and own it.  Small launch tables are always library-owned.
+ *  - Streams: all device work of a context is ordered on the cudaStream_t
+ *    given at creation (NULL = legacy default stream).  lbm_step() is
+ *    asynchronous; calls that return host data synchronise that stream.
+ *  - Host arrays are caller-owned, row-major [ny][nx] (x fastest); DF
+ *    arrays are [9][ny][nx].  Values are FP64 whatever the precision.
+ *  - Storage: DFs are stored as deviations from the rest equilibrium
+ *    f_i - M^-1 m^eq(rho0, u = 0, T0) (and the g analogue), in FP64
+ *    (LBM_FP64) or FP32 (LBM_FP32_DEV); reductions are always FP64.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = -1,     /* bad argument or configuration */
+    LBM_ENOMEM = -2,     /* workspace too small or allocation failed */
+    LBM_ECUDA = -3,      /* a CUDA runtime call failed */
+    LBM_EUNSTABLE = -4,  /* NaN/Inf detected in the state (sticky) */
+    LBM_ETIMEOUT = -5    /* a bounded device wait gave up */
+} lbm_status;
+
+typedef enum { LBM_FP64 = 0, LBM_FP32_DEV = 1 } lbm_precision;
+typedef enum { LBM_WALL_S = 0, LBM_WALL_N = 1, LBM_WALL_W = 2, LBM_WALL_E = 3 } lbm_wall;
+
+/* EOS kinds: Eqs. (EOSs.1), (EOSs.2), (EOSs.3) of Sec. 4 and the cubic
+ * p = rho R T / (1 - b rho) - a rho^2 (params {a, b}).  R is always chosen so
+ * that dp/drho = c_s^2 = 1/3 at (rho0, T0), Eq. (cs). */
+typedef enum { LBM_EOS_DECOUPLING = 0, LBM_EOS_IDEAL = 1, LBM_EOS_CS = 2, LBM_EOS_CUBIC = 3 } lbm_eos;
+
+/* Wall data of one side (Sec. 3).  A periodic side must face a periodic side. */
+typedef struct {
+    int32_t periodic;     /* 1: periodic pair, rest ignored */
+    int32_t thermal;      /* 0 Dirichlet (T given), 1 Neumann (adiabatic, Eq. BB.g) */
+    int32_t extrap_order; /* 1 or 2, Eq. (neq.extrapolation) */
+    int32_t reserved;
+    double u[2];          /* wall velocity */
+    double T;             /* Dirichlet temperature */
+} lbm_wall_bc;
+
+/* Problem statement (Secs. 2-4).  Corner nodes take u = 0, the x-side's
+ * extrapolation order, and a Dirichlet temperature if either side has one
+ * (x-side first). */
+typedef struct {
+    int32_t nx, ny;       /* walled extents need >= 4 nodes, periodic >= 1 */
+    int32_t precision;    /* lbm_precision */
+    int32_t visc_law;     /* 0 constant mu, 1 mu = mu0 T/T0, 2 Sutherland */
+    double rho0, T0;      /* reference state */
+    double Pr;            /* Prandtl number Cp mu / lambda (Sec. 2.2) */
+    double gamma;         /* Cp / Cv with Cp - Cv = p0 / (rho0 T0) */
+    double tau0;          /* 1/s_p at (rho0, T0): mu0 = rho0 (tau0 - 1/2) / 3 */
+    double visc_p[2];     /* Sutherland: visc_p[0] = S / T0 (ratio form of Sec. 4.3) */
+    double bulk_ratio;    /* varsigma / nu (Table 1) */
+    double varpi, gamma1, gamma2; /* Eq. (LBE.u.coefficients), n^eq; paper: 1/6, -2, 2 */
+    int32_t force_mode;   /* 0: F = force; 1: F = rho * force (gravity) */
+    int32_t corrections;  /* 1: keep the R, T, X terms of Eq. (LBE.u.c) */
+    double force[2];
+    lbm_wall_bc wall[4];  /* indexed by lbm_wall */
+} lbm_config;
+
+typedef struct lbm_ctx lbm_ctx;
+typedef struct lbm_batch lbm_batch;
+
+/* Device bytes needed by one context of this configuration. */
+lbm_status lbm_workspace_bytes(const lbm_config* cfg, size_t* bytes);
+
+/* Create a context.  workspace: device pointer (or NULL, see above);
+ * cuda_stream: cudaStream_t or NULL.  *out receives the context. */
+lbm_status lbm_create(const lbm_config* cfg, void* workspace, size_t workspace_bytes,
+                      void* cuda_stream, lbm_ctx** out);
+
+/* Select the EOS (Sec. 2.2 end, Eqs. EOSs, cs, Cp), derive R, Cv, Cp, mu0,
+ * lambda0, and initialise the lattice at rest: f = M^-1 (m^eq - F_m/2),
+ * g = M^-1 (n^eq - Q_m/2) at (rho0, 0, T0) (Eq. decompose, zero
+ * non-equilibrium part).  params: {a, b} (cubic), {b} or none (CS). */
+lbm_status lbm_set_eos(lbm_ctx* ctx, int kind, const double* params, int nparams);
+
+/* Advance nsteps time steps (Eqs. LBE.u, LBE.T, BB.f, BB.g, Sec. 3):
+ * fused collide + stream of every node, then the wall pass.  Async. */
+lbm_status lbm_step(lbm_ctx* ctx, long nsteps);
+
+/* Synchronise the context's stream and return its sticky status. */
+lbm_status lbm_sync(lbm_ctx* ctx);
+
+/* Macroscopic fields (Eqs. rho.u, E; T = eps / Cv; p = p_EOS) into host
+ * arrays [ny][nx]; NULL skips a field.  Synchronises. */
+lbm_status lbm_macros(lbm_ctx* ctx, double* rho, double* ux, double* uy, double* T, double* p);
+
+/* Same into device arrays [ny][nx] (FP64); asynchronous. */
+lbm_status lbm_macros_device(lbm_ctx* ctx, double* rho, double* ux, double* uy, double* T, double* p);
+
+/* Mean Nusselt number through a Dirichlet wall (Sec. 4.3): inward flux
+ * -lambda(T_w) dT/dn (one-sided, second order), trapezoid rule along the
+ * wall over L = N - 1, divided by lambda(T0) (T_max - T_min) over the
+ * Dirichlet walls.  Synchronises. */
+lbm_status lbm_nusselt(lbm_ctx* ctx, int wall, double* nu);
+
+/* FP64 global diagnostics, deterministic order.  out[8] receives:
+ *  0 total mass sum(rho), 1 total energy sum(rho E), 2 p*_ave (trapezoid
+ *  mean of p / p0 over the square, Sec. 4.3), 3 residual
+ *  max(|u - u_snap|_2 / |u|_2, |T - T_snap|_2 / |T - T0|_2) against the
+ *  last snapshot (0 if none), 4 number of non-finite nodes, 5 max |u|,
+ *  6 mean T, 7 steps taken.  snapshot != 0 stores u, T as the new snapshot.
+ *  Synchronises. */
+lbm_status lbm_diagnostics(lbm_ctx* ctx, int snapshot, double* out8);
+
+/* DF state as [9][ny][nx] FP64 host arrays (full values, not deviations). */
+lbm_status lbm_get_state(lbm_ctx* ctx, double* f, double* g);
+lbm_status lbm_set_state(lbm_ctx* ctx, const double* f, const double* g);
+
+/* Equilibrium initialisation from host fields rho, ux, uy, T [ny][nx]. */
+lbm_status lbm_init_macros(lbm_ctx* ctx, const double* rho, const double* ux,
+                           const double* uy, const double* T);
+
+/* Derived constants: R, Cv, Cp, mu0, p0, eta0, lambda0, c_s^2. */
+lbm_status lbm_derived(const lbm_ctx* ctx, double* out8);
+
+/* Launch shape of the fused kernel: strip width bx (64 or 128 threads) and
+ * rows per CTA by (>= 1).  Used by the autotuner. */
+lbm_status lbm_set_tile(lbm_ctx* ctx, int bx, int by);
+
+/* Steps taken since the last (re)initialisation. */
+long lbm_step_count(const lbm_ctx* ctx);
+
+lbm_status lbm_destroy(lbm_ctx* ctx);            /* NULL-safe */
+const char* lbm_last_error(void);
+
+/* Batched stepping: contexts (same stream, any size/EOS/precision mix) are
+ * advanced together, one fused launch per precision and one wall-pass launch
+ * per step.  graph_steps > 0 captures that many steps in a CUDA graph that
+ * lbm_batch_step replays (nsteps must then be a multiple of graph_steps). */
+lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, int graph_steps, lbm_batch** out);
+lbm_status lbm_batch_step(lbm_batch* b, long nsteps);
+lbm_status lbm_batch_destroy(lbm_batch* b);     /* NULL-safe */
+
+/* Same as lbm_batch_step without the graph, with CUDA events recorded on the
+ * batch stream around each step's fused launches and wall-pass launches;
+ * *ms_collide and *ms_wall receive their summed device times.  Synchronises. */
+lbm_status lbm_batch_step_profiled(lbm_batch* b, long nsteps, double* ms_collide, double* ms_wall);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,1387 @@
+// GB300 (sm_103a) kernels and C ABI of the thermal MRT lattice-Boltzmann
+// hot path of arXiv:1809.08683 (declarations and conventions: include/lbm.h).
+//
+// Data layout in HBM, per lattice: two buffers (A, B), each 18 planes
+// (f'_0..f'_8, g'_0..g'_8) of ny rows with a pitch of nx rounded up to 32
+// elements, FP64 or FP32.  One time step is
+//   k_collide_stream : every node is loaded once from the current buffer,
+//                      collided (Eqs. LBE.u.c, LBE.T.c) and pushed into the
+//                      other buffer (Eqs. LBE.u.s, LBE.T.s); a population that
+//                      would leave the domain is written back reversed into the
+//                      node's own slot (Eqs. BB.f, BB.g);
+//   k_boundary       : every wall node of the other buffer is rebuilt from its
+//                      bounced sums, the wall data and the extrapolated
+//                      redefined non-equilibrium moments (Sec. 3).
+// The fused kernel assigns each CTA a strip of BX columns and a run of rows.
+// It sweeps the run row by row, keeping rho' and p' of the rows j-1, j, j+1
+// (plus one halo column on each side) in a shared-memory ring, so the
+// gradients of the correction terms T grad(rho) and X grad(p) need no extra
+// pass over HBM.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_node.cuh"
+
+using lbm::Mac;
+using lbm::Params;
+
+namespace {
+
+// ------------------------------------------------------------------------
+// device-side descriptors
+// ------------------------------------------------------------------------
+
+struct WallDev {
+    double u[2];
+    double T;
+    int thermal;
+    int order;
+};
+
+struct InstDesc {
+    void* buf[2];
+    long long plane;  // elements per plane
+    int nx, ny, pitch, px, py;
+    int precision;
+    unsigned int* status;
+    WallDev wall[4];
+    Params<double> pd;
+    Params<float> pf;
+};
+
+struct Work {  // one CTA of the fused kernel
+    int inst, x0, y0, y1, par, pad0, pad1, pad2;
+};
+
+struct BWork {  // one CTA of the wall pass
+    int inst, k0, cnt, par;
+};
+
+template <typename R>
+__device__ __forceinline__ const Params<R>& dparams(const InstDesc* D);
+template <>
+__device__ __forceinline__ const Params<double>& dparams<double>(const InstDesc* D) { return D->pd; }
+template <>
+__device__ __forceinline__ const Params<float>& dparams<float>(const InstDesc* D) { return D->pf; }
+
+
+template <typename R>
+__device__ __forceinline__ void load18(const R* __restrict__ base, long long plane, long long idx, R* v) {
+#pragma unroll
+    for (int q = 0; q < 18; ++q) v[q] = __ldg(base + q * plane + idx);
+}
+
+template <typename R>
+__device__ __forceinline__ void store18(R* __restrict__ base, long long plane, long long idx, const R* v) {
+#pragma unroll
+    for (int q = 0; q < 18; ++q) base[q * plane + idx] = v[q];
+}
+
+template <typename R>
+__device__ __forceinline__ void node_macros(const Params<R>& P, const R* v, Mac<R>& m) {
+    R rd, jx, jy, sg;
+    lbm::node_sums(v, v + 9, rd, jx, jy, sg);
+    lbm::macros(P, rd, jx, jy, sg, m);
+}
+
+template <typename R>
+__device__ void load_params(Params<R>* dst, const Params<R>* src) {
+    const int n = sizeof(Params<R>) / sizeof(int);
+    const int* s = reinterpret_cast<const int*>(src);
+    int* d = reinterpret_cast<int*>(dst);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = s[i];
+}
+
+// rho' and p' of node (xx, yy) read straight from a buffer.
+template <typename R>
+__device__ void rho_p_at(const Params<R>& P, const R* __restrict__ src, long long plane, int pitch,
+                         int xx, int yy, R& rd, R& pd) {
+    R v[18];
+    load18(src, plane, (long long)yy * pitch + xx, v);
+    Mac<R> m;
+    node_macros(P, v, m);
+    rd = m.rho_d;
+    pd = m.p_d;
+}
+
+// ------------------------------------------------------------------------
+// fused collide + stream
+// ------------------------------------------------------------------------
+
+template <typename R, int BX>
+__global__ void __launch_bounds__(BX) k_collide_stream(const Work* __restrict__ work,
+                                                       InstDesc* const* __restrict__ descs, int step_par) {
+    __shared__ Params<R> P;
+    __shared__ R s_rho[3][BX + 2];
+    __shared__ R s_p[3][BX + 2];
+    const Work w = work[blockIdx.x];
+    const InstDesc* D = descs[w.inst];
+    load_params(&P, &dparams<R>(D));
+    const int nx = D->nx, ny = D->ny, pitch = D->pitch, px = D->px, py = D->py;
+    const long long plane = D->plane;
+    const int b = w.par ^ step_par;
+    const R* __restrict__ src = reinterpret_cast<const R*>(D->buf[b]);
+    R* __restrict__ dst = reinterpret_cast<R*>(D->buf[b ^ 1]);
+    unsigned int* status = D->status;
+    __syncthreads();
+
+    const int tid = threadIdx.x;
+    const int x = w.x0 + tid;
+    const bool active = x < nx;
+    const int xlast = min(w.x0 + BX, nx) - 1;
+    const int tlast = xlast - w.x0;
+    int xhl = w.x0 - 1;
+    bool has_l = true;
+    if (xhl < 0) { if (px) xhl = nx - 1; else has_l = false; }
+    int xhr = xlast + 1;
+    bool has_r = true;
+    if (xhr >= nx) { if (px) xhr = 0; else has_r = false; }
+    const int c = tid + 1;
+
+    // macros of one row into a ring slot; active threads keep their DFs in v
+    auto row_macros = [&](int yy, int slot, R* v, Mac<R>& m) {
+        if (active) {
+            load18(src, plane, (long long)yy * pitch + x, v);
+            node_macros(P, v, m);
+            s_rho[slot][c] = m.rho_d;
+            s_p[slot][c] = m.p_d;
+        }
+        if (tid == 0 && has_l) {
+            R rd, pd;
+            rho_p_at(P, src, plane, pitch, xhl, yy, rd, pd);
+            s_rho[slot][0] = rd;
+            s_p[slot][0] = pd;
+        }
+        if (tid == tlast && has_r) {
+            R rd, pd;
+            rho_p_at(P, src, plane, pitch, xhr, yy, rd, pd);
+            s_rho[slot][tlast + 2] = rd;
+            s_p[slot][tlast + 2] = pd;
+        }
+    };
+
+    R cur[18], nxt[18];
+    Mac<R> mc, mn;
+    {
+        int ym = w.y0 - 1;
+        bool has_m = true;
+        if (ym < 0) { if (py) ym = ny - 1; else has_m = false; }
+        if (has_m) row_macros(ym, 0, nxt, mn);
+        row_macros(w.y0, 1, cur, mc);
+    }
+
+    for (int j = w.y0; j < w.y1; ++j) {
+        const int jl = j - w.y0;
+        const int sm = jl % 3, s0 = (jl + 1) % 3, sp = (jl + 2) % 3;
+        int yn = j + 1;
+        bool has_n = true;
+        if (yn >= ny) { if (py) yn = 0; else has_n = false; }
+        if (has_n) row_macros(yn, sp, nxt, mn);
+        __syncthreads();
+
+        if (active) {
+            if (!(isfinite(mc.rho_d) && isfinite(mc.T_d))) atomicOr(status, 1u);
+            const bool onS = !py && j == 0, onN = !py && j == ny - 1;
+            const bool onW = !px && x == 0, onE = !px && x == nx - 1;
+            R grx, gry, gpx, gpy;
+            if (!(onS || onN || onW || onE)) {
+                // grad = 3 sum_i w_i e_i phi(x + e_i), w = 1/9 (axis), 1/36 (diagonal)
+                const R t = R(1.0 / 3.0), d = R(1.0 / 12.0);
+                grx = t * (s_rho[s0][c + 1] - s_rho[s0][c - 1])
+                    + d * ((s_rho[sp][c + 1] - s_rho[sp][c - 1]) + (s_rho[sm][c + 1] - s_rho[sm][c - 1]));
+                gry = t * (s_rho[sp][c] - s_rho[sm][c])
+                    + d * ((s_rho[sp][c + 1] - s_rho[sm][c + 1]) + (s_rho[sp][c - 1] - s_rho[sm][c - 1]));
+                gpx = t * (s_p[s0][c + 1] - s_p[s0][c - 1])
+                    + d * ((s_p[sp][c + 1] - s_p[sp][c - 1]) + (s_p[sm][c + 1] - s_p[sm][c - 1]));
+                gpy = t * (s_p[sp][c] - s_p[sm][c])
+                    + d * ((s_p[sp][c + 1] - s_p[sm][c + 1]) + (s_p[sp][c - 1] - s_p[sm][c - 1]));
+            } else {
+                // wall node: one-sided second order along the inward normal,
+                // central along the wall
+                const R r0 = s_rho[s0][c], p0 = s_p[s0][c];
+                if (onW || onE) {
+                    const int dx = onW ? 1 : -1;
+                    R r2, p2;
+                    rho_p_at(P, src, plane, pitch, x + 2 * dx, j, r2, p2);
+                    const R r1 = s_rho[s0][c + dx], p1 = s_p[s0][c + dx];
+                    grx = R(dx) * (R(-3) * r0 + R(4) * r1 - r2) * R(0.5);
+                    gpx = R(dx) * (R(-3) * p0 + R(4) * p1 - p2) * R(0.5);
+                } else {
+                    grx = (s_rho[s0][c + 1] - s_rho[s0][c - 1]) * R(0.5);
+                    gpx = (s_p[s0][c + 1] - s_p[s0][c - 1]) * R(0.5);
+                }
+                if (onS || onN) {
+                    const int dy = onS ? 1 : -1;
+                    R r2, p2;
+                    rho_p_at(P, src, plane, pitch, x, j + 2 * dy, r2, p2);
+                    const R r1 = onS ? s_rho[sp][c] : s_rho[sm][c];
+                    const R p1 = onS ? s_p[sp][c] : s_p[sm][c];
+                    gry = R(dy) * (R(-3) * r0 + R(4) * r1 - r2) * R(0.5);
+                    gpy = R(dy) * (R(-3) * p0 + R(4) * p1 - p2) * R(0.5);
+                } else {
+                    gry = (s_rho[sp][c] - s_rho[sm][c]) * R(0.5);
+                    gpy = (s_p[sp][c] - s_p[sm][c]) * R(0.5);
+                }
+            }
+
+            lbm::collide(P, mc, cur, cur + 9, grx, gry, gpx, gpy);
+
+            // push; a population leaving the domain returns reversed to this node
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const int ex = (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+                const int ey = (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+                const int opp = (i == 0) ? 0 : (i <= 4 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5);
+                int xd = x + ex, yd = j + ey;
+                bool out = false;
+                if (xd < 0 || xd >= nx) { if (px) xd = (xd < 0) ? nx - 1 : 0; else out = true; }
+                if (yd < 0 || yd >= ny) { if (py) yd = (yd < 0) ? ny - 1 : 0; else out = true; }
+                if (out) {
+                    const long long o = (long long)j * pitch + x;
+                    dst[opp * plane + o] = cur[i];
+                    dst[(9 + opp) * plane + o] = cur[9 + i];
+                } else {
+                    const long long o = (long long)yd * pitch + xd;
+                    dst[i * plane + o] = cur[i];
+                    dst[(9 + i) * plane + o] = cur[9 + i];
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 18; ++q) cur[q] = nxt[q];
+        mc = mn;
+    }
+}
+
+// ------------------------------------------------------------------------
+// wall pass (Sec. 3)
+// ------------------------------------------------------------------------
+
+struct WallNode {
+    int x, y, dx, dy;  // position and inward normal
+    double ux, uy, T;
+    int thermal, order;
+};
+
+__device__ __host__ inline int wall_count(int nx, int ny, int px, int py) {
+    if (px && py) return 0;
+    if (!py && px) return 2 * nx;
+    if (py && !px) return 2 * ny;
+    return 2 * nx + 2 * (ny - 2);
+}
+
+// k-th wall node: south row, north row, then west and east columns
+// (without the corners when the rows exist).
+__device__ void wall_node(const InstDesc* D, int k, WallNode& n) {
+    const int nx = D->nx, ny = D->ny, px = D->px, py = D->py;
+    int x, y;
+    if (!py) {
+        if (k < nx) { x = k; y = 0; }
+        else if (k < 2 * nx) { x = k - nx; y = ny - 1; }
+        else {
+            int r = k - 2 * nx;
+            if (r < ny - 2) { x = 0; y = r + 1; }
+            else { x = nx - 1; y = r - (ny - 2) + 1; }
+        }
+    } else {
+        if (k < ny) { x = 0; y = k; }
+        else { x = nx - 1; y = k - ny; }
+    }
+    const bool onS = !py && y == 0, onN = !py && y == ny - 1;
+    const bool onW = !px && x == 0, onE = !px && x == nx - 1;
+    n.x = x;
+    n.y = y;
+    n.dx = onW ? 1 : (onE ? -1 : 0);
+    n.dy = onS ? 1 : (onN ? -1 : 0);
+    const WallDev* ws = onS ? &D->wall[0] : (onN ? &D->wall[1] : nullptr);
+    const WallDev* wx = onW ? &D->wall[2] : (onE ? &D->wall[3] : nullptr);
+    if (ws && wx) {
+        // corner: at rest, x-side order, Dirichlet wins (x-side first)
+        n.ux = 0.0;
+        n.uy = 0.0;
+        n.order = wx->order;
+        if (wx->thermal == 0) { n.thermal = 0; n.T = wx->T; }
+        else if (ws->thermal == 0) { n.thermal = 0; n.T = ws->T; }
+        else { n.thermal = 1; n.T = 0.0; }
+    } else {
+        const WallDev* ww = ws ? ws : wx;
+        n.ux = ww->u[0];
+        n.uy = ww->u[1];
+        n.thermal = ww->thermal;
+        n.T = ww->T;
+        n.order = ww->order;
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_boundary(const BWork* __restrict__ work,
+                                                  InstDesc* const* __restrict__ descs, int step_par) {
+    __shared__ Params<R> P;
+    const BWork w = work[blockIdx.x];
+    const InstDesc* D = descs[w.inst];
+    load_params(&P, &dparams<R>(D));
+    __syncthreads();
+    if ((int)threadIdx.x >= w.cnt) return;
+    const int k = w.k0 + threadIdx.x;
+    const int pitch = D->pitch;
+    const long long plane = D->plane;
+    R* __restrict__ buf = reinterpret_cast<R*>(D->buf[(w.par ^ step_par) ^ 1]);
+    WallNode n;
+    wall_node(D, k, n);
+
+    // density (and Neumann total energy) from the bounced-back populations
+    R v[18];
+    const long long ib = (long long)n.y * pitch + n.x;
+    load18<R>(buf, plane, ib, v);
+    R rd, jx, jy, sg;
+    lbm::node_sums(v, v + 9, rd, jx, jy, sg);
+    const R ux = R(n.ux), uy = R(n.uy);
+    Mac<R> mb;
+    R rhoE_d;
+    if (n.thermal == 0) {
+        const R Td = R(n.T) - P.T0;
+        const R Ed = P.Cv * Td + R(0.5) * (ux * ux + uy * uy);
+        rhoE_d = rd * P.E0 + (P.rho0 + rd) * Ed;
+    } else {
+        const R rho = P.rho0 + rd;
+        const R Fx = P.force_mode ? rho * P.Fx : P.Fx;
+        const R Fy = P.force_mode ? rho * P.Fy : P.Fy;
+        rhoE_d = sg + R(0.5) * (ux * Fx + uy * Fy);
+    }
+    lbm::wall_macros(P, rd, ux, uy, rhoE_d, mb);
+
+    // redefined non-equilibrium moments at x_f (and x_ff), extrapolated
+    R mt[9], nt[9];
+    {
+        R u[18];
+        Mac<R> m;
+        load18<R>(buf, plane, (long long)(n.y + n.dy) * pitch + (n.x + n.dx), u);
+        node_macros(P, u, m);
+        lbm::tilde_neq(P, m, u, u + 9, mt, nt);
+        if (n.order == 2) {
+            R mt2[9], nt2[9];
+            load18<R>(buf, plane, (long long)(n.y + 2 * n.dy) * pitch + (n.x + 2 * n.dx), u);
+            node_macros(P, u, m);
+            lbm::tilde_neq(P, m, u, u + 9, mt2, nt2);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                mt[q] = R(2) * mt[q] - mt2[q];
+                nt[q] = R(2) * nt[q] - nt2[q];
+            }
+        }
+    }
+    lbm::rebuild(P, mb, mt, nt, v, v + 9);
+    store18<R>(buf, plane, ib, v);
+}
+
+// ------------------------------------------------------------------------
+// initialisation, state transfer, macros, reductions
+// ------------------------------------------------------------------------
+
+template <typename R>
+__global__ void k_init_rest(const InstDesc* D, int b) {
+    const Params<R>& P = dparams<R>(D);
+    const long long nn = (long long)D->nx * D->ny;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(t / D->nx), x = (int)(t % D->nx);
+        Mac<R> m;
+        lbm::wall_macros(P, R(0), R(0), R(0), R(0), m);
+        R v[18];
+        lbm::equilibrium(P, m, v, v + 9);
+        store18<R>(reinterpret_cast<R*>(D->buf[b]), D->plane, (long long)y * D->pitch + x, v);
+    }
+}
+
+template <typename R>
+__global__ void k_init_macros(const InstDesc* D, int b, const double* __restrict__ rho,
+                              const double* __restrict__ ux, const double* __restrict__ uy,
+                              const double* __restrict__ T) {
+    const Params<double>& Pd = D->pd;
+    const Params<R>& P = dparams<R>(D);
+    const long long nn = (long long)D->nx * D->ny;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(t / D->nx), x = (int)(t % D->nx);
+        const double rd = rho[t] - Pd.rho0;
+        const double u = ux[t], vv = uy[t];
+        const double Ed = Pd.Cv * (T[t] - Pd.T0) + 0.5 * (u * u + vv * vv);
+        const double rhoE_d = rd * Pd.E0 + rho[t] * Ed;
+        Mac<R> m;
+        lbm::wall_macros(P, R(rd), R(u), R(vv), R(rhoE_d), m);
+        R v[18];
+        lbm::equilibrium(P, m, v, v + 9);
+        store18<R>(reinterpret_cast<R*>(D->buf[b]), D->plane, (long long)y * D->pitch + x, v);
+    }
+}
+
+// plane q of buffer b <-> dense FP64 array [ny][nx] of full values (deviation + rest)
+template <typename R>
+__global__ void k_get_plane(const InstDesc* D, int b, int q, double rest, double* __restrict__ out) {
+    const long long nn = (long long)D->nx * D->ny;
+    const R* base = reinterpret_cast<const R*>(D->buf[b]) + q * D->plane;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(t / D->nx), x = (int)(t % D->nx);
+        out[t] = (double)base[(long long)y * D->pitch + x] + rest;
+    }
+}
+
+template <typename R>
+__global__ void k_set_plane(const InstDesc* D, int b, int q, double rest, const double* __restrict__ in) {
+    const long long nn = (long long)D->nx * D->ny;
+    R* base = reinterpret_cast<R*>(D->buf[b]) + q * D->plane;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(t / D->nx), x = (int)(t % D->nx);
+        base[(long long)y * D->pitch + x] = (R)(in[t] - rest);
+    }
+}
+
+// FP64 macros of one node of an R-typed buffer.
+template <typename R>
+__device__ __forceinline__ void macros_fp64(const InstDesc* D, const R* buf, int x, int y, Mac<double>& m) {
+    R v[18];
+    load18(buf, D->plane, (long long)y * D->pitch + x, v);
+    double w[18];
+#pragma unroll
+    for (int q = 0; q < 18; ++q) w[q] = (double)v[q];
+    double rd, jx, jy, sg;
+    lbm::node_sums(w, w + 9, rd, jx, jy, sg);
+    lbm::macros(D->pd, rd, jx, jy, sg, m);
+}
+
+template <typename R>
+__global__ void k_macros(const InstDesc* D, int b, double* rho, double* ux, double* uy, double* T,
+                         double* p) {
+    const long long nn = (long long)D->nx * D->ny;
+    const R* buf = reinterpret_cast<const R*>(D->buf[b]);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(t / D->nx), x = (int)(t % D->nx);
+        Mac<double> m;
+        macros_fp64(D, buf, x, y, m);
+        if (rho) rho[t] = m.rho;
+        if (ux) ux[t] = m.ux;
+        if (uy) uy[t] = m.uy;
+        if (T) T[t] = m.T;
+        if (p) p[t] = D->pd.p0 + m.p_d;
+    }
+}
+
+constexpr int kDiagSlots = 10;
+constexpr int kDiagBlocks = 304;   // 2 per SM on a 152-SM part; fixed for a deterministic order
+constexpr int kDiagThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Per-block FP64 partial sums (slot 8 is a maximum) into partials[block][kDiagSlots].
+template <typename R>
+__global__ void __launch_bounds__(kDiagThreads) k_diag(const InstDesc* D, int b, double* __restrict__ snap,
+                                                       int take_snapshot, int have_snapshot,
+                                                       double* __restrict__ partials) {
+    const long long nn = (long long)D->nx * D->ny;
+    const R* buf = reinterpret_cast<const R*>(D->buf[b]);
+    double acc[kDiagSlots];
+#pragma unroll
+    for (int s = 0; s < kDiagSlots; ++s) acc[s] = 0.0;
+    const double Lx = D->px ? (double)D->nx : (double)(D->nx - 1);
+    const double Ly = D->py ? (double)D->ny : (double)(D->ny - 1);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(t / D->nx), x = (int)(t % D->nx);
+        Mac<double> m;
+        macros_fp64(D, buf, x, y, m);
+        const bool bad = !(isfinite(m.rho) && isfinite(m.T) && isfinite(m.ux) && isfinite(m.uy));
+        if (bad) { acc[7] += 1.0; continue; }
+        const double wx = (!D->px && (x == 0 || x == D->nx - 1)) ? 0.5 : 1.0;
+        const double wy = (!D->py && (y == 0 || y == D->ny - 1)) ? 0.5 : 1.0;
+        const double p = D->pd.p0 + m.p_d;
+        acc[0] += m.rho_d;
+        acc[1] += m.rhoE_d;
+        acc[2] += wx * wy * p / (D->pd.p0 * Lx * Ly);
+        const double u2 = m.ux * m.ux + m.uy * m.uy;
+        if (have_snapshot) {
+            const double dux = m.ux - snap[t], duy = m.uy - snap[nn + t], dT = m.T - snap[2 * nn + t];
+            acc[3] += dux * dux + duy * duy;
+            acc[5] += dT * dT;
+        }
+        acc[4] += u2;
+        acc[6] += m.T_d * m.T_d;
+        acc[8] = fmax(acc[8], sqrt(u2));
+        acc[9] += m.T;
+        if (take_snapshot) {
+            snap[t] = m.ux;
+            snap[nn + t] = m.uy;
+            snap[2 * nn + t] = m.T;
+        }
+    }
+    __shared__ double red[kDiagThreads / 32][kDiagSlots];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int s = 0; s < kDiagSlots; ++s) {
+        const double v = (s == 8) ? warp_max(acc[s]) : warp_sum(acc[s]);
+        if (lane == 0) red[wid][s] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kDiagSlots) {
+        const int s = threadIdx.x;
+        double v = red[0][s];
+        for (int k = 1; k < kDiagThreads / 32; ++k) v = (s == 8) ? fmax(v, red[k][s]) : v + red[k][s];
+        partials[blockIdx.x * kDiagSlots + s] = v;
+    }
+}
+
+__global__ void k_diag_final(const double* __restrict__ partials, int nblocks, double* __restrict__ out) {
+    const int s = threadIdx.x;
+    if (s >= kDiagSlots) return;
+    double v = 0.0;
+    for (int k = 0; k < nblocks; ++k) v = (s == 8) ? fmax(v, partials[k * kDiagSlots + s]) : v + partials[k * kDiagSlots + s];
+    out[s] = v;
+}
+
+// Mean Nusselt number through one wall: one block, fixed-order tree.
+template <typename R>
+__global__ void __launch_bounds__(1024) k_nusselt(const InstDesc* D, int b, int wall, double dT, double* out) {
+    const R* buf = reinterpret_cast<const R*>(D->buf[b]);
+    const int nx = D->nx, ny = D->ny;
+    const int len = (wall >= 2) ? ny : nx;
+    const Params<double>& P = D->pd;
+    double acc = 0.0;
+    for (int t = threadIdx.x; t < len; t += blockDim.x) {
+        int x0, y0, dx, dy;
+        if (wall == 0) { x0 = t; y0 = 0; dx = 0; dy = 1; }
+        else if (wall == 1) { x0 = t; y0 = ny - 1; dx = 0; dy = -1; }
+        else if (wall == 2) { x0 = 0; y0 = t; dx = 1; dy = 0; }
+        else { x0 = nx - 1; y0 = t; dx = -1; dy = 0; }
+        Mac<double> m0, m1, m2;
+        macros_fp64(D, buf, x0, y0, m0);
+        macros_fp64(D, buf, x0 + dx, y0 + dy, m1);
+        macros_fp64(D, buf, x0 + 2 * dx, y0 + 2 * dy, m2);
+        const double dTdn = (-3.0 * m0.T + 4.0 * m1.T - m2.T) * 0.5;
+        const double lam = P.lam_fac * lbm::viscosity(P, m0.T);
+        const double wgt = (t == 0 || t == len - 1) ? 0.5 : 1.0;
+        acc += wgt * (-lam * dTdn);
+    }
+    __shared__ double red[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    acc = warp_sum(acc);
+    if (lane == 0) red[wid] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) v += red[k];
+        const double lam0 = P.lam_fac * P.mu0;
+        out[0] = v / (lam0 * dT);
+    }
+}
+
+// ------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------
+
+thread_local std::string g_err;
+
+lbm_status fail(lbm_status st, const std::string& msg) {
+    g_err = msg;
+    return st;
+}
+
+#define CUDA_TRY(call)                                                                       \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(LBM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));      \
+    } while (0)
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Layout {
+    size_t off_desc, off_descs, off_status, off_diag, off_partials, off_bufA, off_bufB, off_snap, off_stage;
+    size_t total, buf_bytes;
+    int pitch;
+    long long plane;
+};
+
+Layout layout_for(const lbm_config& c) {
+    Layout L{};
+    const size_t es = c.precision == LBM_FP32_DEV ? 4 : 8;
+    L.pitch = (int)align_up((size_t)c.nx, 32);
+    L.plane = (long long)L.pitch * c.ny;
+    const size_t nn = (size_t)c.nx * c.ny;
+    size_t o = 0;
+    L.off_desc = o; o = align_up(o + sizeof(InstDesc), 256);
+    L.off_descs = o; o = align_up(o + sizeof(void*), 256);
+    L.off_status = o; o = align_up(o + 256, 256);
+    L.off_diag = o; o = align_up(o + 16 * sizeof(double), 256);
+    L.off_partials = o; o = align_up(o + (size_t)kDiagBlocks * kDiagSlots * sizeof(double), 256);
+    L.buf_bytes = align_up((size_t)18 * L.plane * es, 256);
+    L.off_bufA = o; o += L.buf_bytes;
+    L.off_bufB = o; o += L.buf_bytes;
+    L.off_snap = o; o = align_up(o + 3 * nn * sizeof(double), 256);
+    L.off_stage = o; o = align_up(o + 5 * nn * sizeof(double), 256);
+    L.total = o;
+    return L;
+}
+
+lbm_status validate(const lbm_config* c) {
+    if (!c) return fail(LBM_EINVAL, "null config");
+    const int px = c->wall[LBM_WALL_W].periodic != 0, pxe = c->wall[LBM_WALL_E].periodic != 0;
+    const int py = c->wall[LBM_WALL_S].periodic != 0, pyn = c->wall[LBM_WALL_N].periodic != 0;
+    if (px != pxe || py != pyn) return fail(LBM_EINVAL, "a periodic side must face a periodic side");
+    if (c->nx < 1 || c->ny < 1) return fail(LBM_EINVAL, "nx, ny must be >= 1");
+    if ((!px && c->nx < 4) || (!py && c->ny < 4)) return fail(LBM_EINVAL, "walled extents need >= 4 nodes");
+    if ((long long)c->nx * c->ny > (1LL << 31)) return fail(LBM_EINVAL, "lattice too large");
+    if (c->precision != LBM_FP64 && c->precision != LBM_FP32_DEV) return fail(LBM_EINVAL, "bad precision");
+    for (int s = 0; s < 4; ++s) {
+        if (c->wall[s].periodic) continue;
+        if (c->wall[s].extrap_order != 1 && c->wall[s].extrap_order != 2)
+            return fail(LBM_EINVAL, "extrap_order must be 1 or 2");
+        if (c->wall[s].thermal != 0 && c->wall[s].thermal != 1) return fail(LBM_EINVAL, "thermal must be 0 or 1");
+    }
+    if (!(c->tau0 > 0.5) || !(c->rho0 > 0) || !(c->T0 > 0) || !(c->gamma > 1.0) || !(c->Pr > 0))
+        return fail(LBM_EINVAL, "need tau0 > 1/2, rho0, T0, Pr > 0, gamma > 1");
+    if (!(c->varpi > 0 && c->varpi < 1.0 / 3.0)) return fail(LBM_EINVAL, "varpi must lie in (0, 1/3)");
+    if (!(c->bulk_ratio > 0)) return fail(LBM_EINVAL, "bulk_ratio must be > 0");
+    if (c->visc_law < 0 || c->visc_law > 2) return fail(LBM_EINVAL, "bad visc_law");
+    return LBM_OK;
+}
+
+template <typename A, typename B>
+void convert_params(const Params<A>& a, Params<B>& b) {
+#define CP(f) b.f = (B)a.f
+    CP(rho0); CP(T0); CP(E0); CP(Cv); CP(inv_Cv); CP(Rg); CP(eos_a); CP(eos_b); CP(p0); CP(rho0E0_p0);
+    CP(rho0Cp0); CP(mu0); CP(inv_T0); CP(visc_S); CP(lam_fac); CP(tj_fac); CP(e_fac); CP(alpha1);
+    CP(beta1); CP(alpha2); CP(beta2); CP(kk); CP(hh); CP(bb); CP(gamma1); CP(gamma2); CP(cR11);
+    CP(cR17); CP(cR18); CP(cR71); CP(cR77); CP(cR81); CP(cR88); CP(Fx); CP(Fy); CP(cs_b0);
+#undef CP
+    b.eos = a.eos;
+    b.visc = a.visc;
+    b.force_mode = a.force_mode;
+    b.corrections = a.corrections;
+}
+
+// f = M^-1 m (host, FP64) for the rest equilibria.
+void host_inverse_moments(const double* m, double* f) { lbm::inverse_moments<double>(m, f); }
+
+}  // namespace
+
+struct lbm_ctx {
+    lbm_config cfg;
+    cudaStream_t stream = nullptr;
+    bool own_ws = false;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    Layout L{};
+    InstDesc h{};
+    InstDesc* d_desc = nullptr;
+    InstDesc** d_descs = nullptr;
+    unsigned int* d_status = nullptr;
+    double* d_diag = nullptr;
+    double* d_partials = nullptr;
+    double* d_snap = nullptr;
+    double* d_stage = nullptr;
+    Work* d_work = nullptr;
+    int n_work = 0, bx = 128, by = 0;
+    BWork* d_bwork = nullptr;
+    int n_bwork = 0;
+    long steps = 0;
+    bool eos_set = false, have_snap = false;
+    lbm_status sticky = LBM_OK;
+    double derived[8] = {0};
+    double f_rest[9] = {0}, g_rest[9] = {0};
+    std::vector<Work> h_work;
+    std::vector<BWork> h_bwork;
+};
+
+struct lbm_batch {
+    std::vector<lbm_ctx*> ctxs;
+    cudaStream_t stream = nullptr;
+    InstDesc** d_descs = nullptr;
+    Work* d_work = nullptr;
+    BWork* d_bwork = nullptr;
+    // launch groups: [precision][bx index] ranges of d_work; [precision] ranges of d_bwork
+    int w_off[2][2] = {{0, 0}, {0, 0}}, w_cnt[2][2] = {{0, 0}, {0, 0}};
+    int b_off[2] = {0, 0}, b_cnt[2] = {0, 0};
+    long steps = 0;
+    int graph_steps = 0;
+    cudaGraphExec_t graph = nullptr;
+};
+
+namespace {
+
+std::vector<Work> make_work(const lbm_config& c, int inst, int bx, int by, int par) {
+    std::vector<Work> v;
+    for (int y0 = 0; y0 < c.ny; y0 += by)
+        for (int x0 = 0; x0 < c.nx; x0 += bx) {
+            Work w{};
+            w.inst = inst;
+            w.x0 = x0;
+            w.y0 = y0;
+            w.y1 = std::min(y0 + by, c.ny);
+            w.par = par;
+            v.push_back(w);
+        }
+    return v;
+}
+
+std::vector<BWork> make_bwork(const lbm_config& c, int inst, int par) {
+    std::vector<BWork> v;
+    const int px = c.wall[LBM_WALL_W].periodic != 0, py = c.wall[LBM_WALL_S].periodic != 0;
+    const int n = wall_count(c.nx, c.ny, px, py);
+    for (int k0 = 0; k0 < n; k0 += 128) {
+        BWork b{};
+        b.inst = inst;
+        b.k0 = k0;
+        b.cnt = std::min(128, n - k0);
+        b.par = par;
+        v.push_back(b);
+    }
+    return v;
+}
+
+int default_rows(const lbm_config& c, int bx) {
+    // enough CTAs to cover 152 SMs several times, runs of at most 64 rows
+    const long long strips = (c.nx + bx - 1) / bx;
+    long long by = 64;
+    while (by > 4 && strips * ((c.ny + by - 1) / by) < 4 * 152) by /= 2;
+    return (int)std::max<long long>(1, std::min<long long>(by, c.ny));
+}
+
+lbm_status upload_work(lbm_ctx* c) {
+    if (c->d_work) { cudaFree(c->d_work); c->d_work = nullptr; }
+    c->h_work = make_work(c->cfg, 0, c->bx, c->by, 0);
+    c->n_work = (int)c->h_work.size();
+    CUDA_TRY(cudaMalloc(&c->d_work, c->h_work.size() * sizeof(Work)));
+    CUDA_TRY(cudaMemcpyAsync(c->d_work, c->h_work.data(), c->h_work.size() * sizeof(Work),
+                             cudaMemcpyHostToDevice, c->stream));
+    return LBM_OK;
+}
+
+template <typename R>
+void launch_collide(const Work* work, int n, int bx, InstDesc* const* descs, int par, cudaStream_t s) {
+    if (n <= 0) return;
+    if (bx == 64) k_collide_stream<R, 64><<<n, 64, 0, s>>>(work, descs, par);
+    else k_collide_stream<R, 128><<<n, 128, 0, s>>>(work, descs, par);
+}
+
+template <typename R>
+void launch_boundary(const BWork* work, int n, InstDesc* const* descs, int par, cudaStream_t s) {
+    if (n <= 0) return;
+    k_boundary<R><<<n, 128, 0, s>>>(work, descs, par);
+}
+
+int grid_for(long long nn) {
+    long long g = (nn + 255) / 256;
+    return (int)std::max<long long>(1, std::min<long long>(g, 152 * 8));
+}
+
+lbm_status check_launch() {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(LBM_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+lbm_status read_status(lbm_ctx* c) {
+    unsigned int st = 0;
+    CUDA_TRY(cudaMemcpyAsync(&st, c->d_status, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (st & 1u) {
+        c->sticky = LBM_EUNSTABLE;
+        return fail(LBM_EUNSTABLE, "non-finite density or temperature detected");
+    }
+    return LBM_OK;
+}
+
+bool is_fp32(const lbm_ctx* c) { return c->cfg.precision == LBM_FP32_DEV; }
+
+int cur_buf(const lbm_ctx* c) { return (int)(c->steps & 1); }
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_last_error(void) { return g_err.c_str(); }
+
+lbm_status lbm_workspace_bytes(const lbm_config* cfg, size_t* bytes) {
+    lbm_status st = validate(cfg);
+    if (st != LBM_OK) return st;
+    if (!bytes) return fail(LBM_EINVAL, "null bytes");
+    *bytes = layout_for(*cfg).total;
+    return LBM_OK;
+}
+
+lbm_status lbm_create(const lbm_config* cfg, void* workspace, size_t workspace_bytes, void* cuda_stream,
+                      lbm_ctx** out) {
+    if (!out) return fail(LBM_EINVAL, "null out");
+    *out = nullptr;
+    lbm_status st = validate(cfg);
+    if (st != LBM_OK) return st;
+    lbm_ctx* c = new lbm_ctx();
+    c->cfg = *cfg;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->L = layout_for(*cfg);
+    if (workspace) {
+        if (workspace_bytes < c->L.total || ((uintptr_t)workspace & 255u)) {
+            delete c;
+            return fail(LBM_ENOMEM, "workspace too small or not 256-byte aligned");
+        }
+        c->ws = (char*)workspace;
+        c->ws_bytes = workspace_bytes;
+    } else {
+        cudaError_t e = cudaMalloc(&c->ws, c->L.total);
+        if (e != cudaSuccess) {
+            delete c;
+            return fail(LBM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+        c->own_ws = true;
+        c->ws_bytes = c->L.total;
+    }
+    c->d_desc = (InstDesc*)(c->ws + c->L.off_desc);
+    c->d_descs = (InstDesc**)(c->ws + c->L.off_descs);
+    c->d_status = (unsigned int*)(c->ws + c->L.off_status);
+    c->d_diag = (double*)(c->ws + c->L.off_diag);
+    c->d_partials = (double*)(c->ws + c->L.off_partials);
+    c->d_snap = (double*)(c->ws + c->L.off_snap);
+    c->d_stage = (double*)(c->ws + c->L.off_stage);
+
+    InstDesc& h = c->h;
+    h.buf[0] = c->ws + c->L.off_bufA;
+    h.buf[1] = c->ws + c->L.off_bufB;
+    h.plane = c->L.plane;
+    h.nx = cfg->nx;
+    h.ny = cfg->ny;
+    h.pitch = c->L.pitch;
+    h.px = cfg->wall[LBM_WALL_W].periodic != 0;
+    h.py = cfg->wall[LBM_WALL_S].periodic != 0;
+    h.precision = cfg->precision;
+    h.status = c->d_status;
+    for (int s = 0; s < 4; ++s) {
+        h.wall[s].u[0] = cfg->wall[s].u[0];
+        h.wall[s].u[1] = cfg->wall[s].u[1];
+        h.wall[s].T = cfg->wall[s].T;
+        h.wall[s].thermal = cfg->wall[s].thermal;
+        h.wall[s].order = cfg->wall[s].extrap_order;
+    }
+    auto cleanup = [&](lbm_status s) {
+        lbm_destroy(c);
+        return s;
+    };
+    if (cudaMemsetAsync(c->d_status, 0, 256, c->stream) != cudaSuccess) return cleanup(fail(LBM_ECUDA, "memset"));
+    InstDesc* p = c->d_desc;
+    if (cudaMemcpyAsync(c->d_descs, &p, sizeof(p), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+        return cleanup(fail(LBM_ECUDA, "descs upload"));
+    c->bx = 128;
+    c->by = default_rows(*cfg, c->bx);
+    if ((st = upload_work(c)) != LBM_OK) return cleanup(st);
+    c->h_bwork = make_bwork(*cfg, 0, 0);
+    c->n_bwork = (int)c->h_bwork.size();
+    if (c->n_bwork) {
+        if (cudaMalloc(&c->d_bwork, c->h_bwork.size() * sizeof(BWork)) != cudaSuccess)
+            return cleanup(fail(LBM_ENOMEM, "cudaMalloc wall table"));
+        if (cudaMemcpyAsync(c->d_bwork, c->h_bwork.data(), c->h_bwork.size() * sizeof(BWork),
+                            cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+            return cleanup(fail(LBM_ECUDA, "wall table upload"));
+    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cleanup(fail(LBM_ECUDA, "sync"));
+    *out = c;
+    return LBM_OK;
+}
+
+lbm_status lbm_destroy(lbm_ctx* c) {
+    if (!c) return LBM_OK;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    if (c->d_work) cudaFree(c->d_work);
+    if (c->d_bwork) cudaFree(c->d_bwork);
+    if (c->own_ws && c->ws) cudaFree(c->ws);
+    delete c;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_eos(lbm_ctx* c, int kind, const double* params, int np) {
+    if (!c) return fail(LBM_EINVAL, "null ctx");
+    if (kind < 0 || kind > 3) return fail(LBM_EINVAL, "bad EOS kind");
+    const lbm_config& k = c->cfg;
+    Params<double> P{};
+    double a = 0.0, b = 0.0;
+    if (kind == LBM_EOS_CS) b = (np >= 1 && params) ? params[0] : std::sqrt(2.0) * M_PI / (3.0 * k.rho0);
+    if (kind == LBM_EOS_CUBIC) {
+        if (np < 2 || !params) return fail(LBM_EINVAL, "cubic EOS needs {a, b}");
+        a = params[0];
+        b = params[1];
+        if (!(b * k.rho0 < 1.0)) return fail(LBM_EINVAL, "cubic EOS needs b rho0 < 1");
+    }
+    // R from dp/drho = c_s^2 = 1/3 at (rho0, T0), Eq. (cs)
+    const double cs2 = 1.0 / 3.0, r0 = k.rho0, T0 = k.T0;
+    double Rg, p0;
+    switch (kind) {
+    case LBM_EOS_DECOUPLING:
+    case LBM_EOS_IDEAL:
+        Rg = cs2 / T0;
+        p0 = r0 * Rg * T0;
+        break;
+    case LBM_EOS_CS: {
+        const double e = b * r0 / 4.0;
+        const double om = 1.0 - e;
+        // d(rho Z)/d rho = (1 + 4e + 4e^2 - 4e^3 + e^4) / (1 - e)^4
+        const double dphi = (1.0 + 4.0 * e + 4.0 * e * e - 4.0 * e * e * e + e * e * e * e) / (om * om * om * om);
+        Rg = cs2 / (dphi * T0);
+        const double Z = (1.0 + e + e * e - e * e * e) / (om * om * om);
+        p0 = Z * r0 * Rg * T0;
+        break;
+    }
+    default: {
+        const double om = 1.0 - b * r0;
+        Rg = (cs2 + 2.0 * a * r0) * om * om / T0;
+        p0 = r0 * Rg * T0 / om - a * r0 * r0;
+        break;
+    }
+    }
+    if (!(Rg > 0)) return fail(LBM_EINVAL, "EOS gives a non-positive gas constant");
+    const double Cv = (p0 / (r0 * T0)) / (k.gamma - 1.0);
+    const double Cp = k.gamma * Cv;
+    const double w = k.varpi;
+    P.rho0 = r0;
+    P.T0 = T0;
+    P.Cv = Cv;
+    P.inv_Cv = 1.0 / Cv;
+    P.E0 = Cv * T0;
+    P.Rg = Rg;
+    P.eos_a = a;
+    P.eos_b = b;
+    P.p0 = p0;
+    P.rho0E0_p0 = r0 * P.E0 + p0;
+    P.rho0Cp0 = r0 * Cp;
+    P.mu0 = r0 * (k.tau0 - 0.5) * cs2;
+    P.inv_T0 = 1.0 / T0;
+    P.visc_S = k.visc_p[0];
+    P.lam_fac = Cp / k.Pr;
+    const double coef = 2.0 / 3.0 + k.gamma1 / 2.0 + k.gamma2 / 3.0;
+    if (!(coef > 0)) return fail(LBM_EINVAL, "gamma1, gamma2 give a non-positive conductivity factor");
+    P.tj_fac = 1.0 / (coef * r0 * Cp);
+    P.e_fac = 3.0 * k.bulk_ratio / w;
+    P.alpha1 = -1.0;
+    P.beta1 = 1.0;
+    P.alpha2 = -(2.0 * P.alpha1 + w + 1.0) / (1.0 - w);
+    P.beta2 = -2.0 * P.beta1 / (1.0 - w);
+    P.kk = 1.0 - w;
+    P.hh = 6.0 * w * (1.0 - w) / (1.0 - 3.0 * w);
+    P.bb = (1.0 - w) / (1.0 - 3.0 * w);
+    P.gamma1 = k.gamma1;
+    P.gamma2 = k.gamma2;
+    P.cR11 = -(9.0 - 15.0 * P.kk - 2.0 * P.hh) / (4.0 * w);
+    P.cR17 = -3.0 * (9.0 - 3.0 * P.kk + 2.0 * P.hh) / 4.0;
+    P.cR18 = 12.0 * (3.0 * P.kk + P.hh);
+    P.cR71 = -(3.0 - 4.0 * P.bb) / (4.0 * w);
+    P.cR77 = -3.0 * (3.0 + 4.0 * P.bb) / 4.0;
+    P.cR81 = P.bb / w;
+    P.cR88 = 6.0 * P.bb;
+    P.Fx = k.force[0];
+    P.Fy = k.force[1];
+    P.cs_b0 = 1.0 - b * r0;
+    P.eos = kind;
+    P.visc = k.visc_law;
+    P.force_mode = k.force_mode;
+    P.corrections = k.corrections;
+    c->h.pd = P;
+    convert_params(P, c->h.pf);
+
+    const double eta0 = (p0 / cs2 - (2.0 + P.alpha1) * r0) / P.beta1;
+    const double mr[9] = {r0, 2.0 * P.alpha1 * r0 + 2.0 * P.beta1 * eta0, P.alpha2 * r0 + P.beta2 * eta0, 0, 0, 0, 0, 0, 0};
+    const double re = r0 * P.E0, rc = r0 * Cp * T0;
+    const double nr[9] = {re, -4.0 * (re - rc) + k.gamma1 * rc, 4.0 * (re - rc) + k.gamma2 * rc, 0, 0, 0, 0, 0, 0};
+    host_inverse_moments(mr, c->f_rest);
+    host_inverse_moments(nr, c->g_rest);
+    c->derived[0] = Rg;
+    c->derived[1] = Cv;
+    c->derived[2] = Cp;
+    c->derived[3] = P.mu0;
+    c->derived[4] = p0;
+    c->derived[5] = eta0;
+    c->derived[6] = Cp * P.mu0 / k.Pr;
+    c->derived[7] = cs2;
+
+    CUDA_TRY(cudaMemcpyAsync(c->d_desc, &c->h, sizeof(InstDesc), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaMemsetAsync(c->d_status, 0, 256, c->stream));
+    c->steps = 0;
+    c->have_snap = false;
+    c->sticky = LBM_OK;
+    const long long nn = (long long)k.nx * k.ny;
+    if (is_fp32(c)) k_init_rest<float><<<grid_for(nn), 256, 0, c->stream>>>(c->d_desc, 0);
+    else k_init_rest<double><<<grid_for(nn), 256, 0, c->stream>>>(c->d_desc, 0);
+    lbm_status st = check_launch();
+    if (st != LBM_OK) return st;
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->eos_set = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_derived(const lbm_ctx* c, double* out8) {
+    if (!c || !out8 || !c->eos_set) return fail(LBM_EINVAL, "context not initialised");
+    memcpy(out8, c->derived, sizeof(c->derived));
+    return LBM_OK;
+}
+
+lbm_status lbm_set_tile(lbm_ctx* c, int bx, int by) {
+    if (!c) return fail(LBM_EINVAL, "null ctx");
+    if (bx != 64 && bx != 128) return fail(LBM_EINVAL, "bx must be 64 or 128");
+    if (by < 1) return fail(LBM_EINVAL, "by must be >= 1");
+    c->bx = bx;
+    c->by = std::min(by, c->cfg.ny);
+    lbm_status st = upload_work(c);
+    if (st != LBM_OK) return st;
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+long lbm_step_count(const lbm_ctx* c) { return c ? c->steps : -1; }
+
+lbm_status lbm_step(lbm_ctx* c, long nsteps) {
+    if (!c || !c->eos_set) return fail(LBM_EINVAL, "context not initialised");
+    if (nsteps < 0) return fail(LBM_EINVAL, "nsteps < 0");
+    if (c->sticky != LBM_OK) return fail(c->sticky, "context is unstable");
+    for (long s = 0; s < nsteps; ++s) {
+        const int par = (int)((c->steps + s) & 1);
+        if (is_fp32(c)) {
+            launch_collide<float>(c->d_work, c->n_work, c->bx, c->d_descs, par, c->stream);
+            launch_boundary<float>(c->d_bwork, c->n_bwork, c->d_descs, par, c->stream);
+        } else {
+            launch_collide<double>(c->d_work, c->n_work, c->bx, c->d_descs, par, c->stream);
+            launch_boundary<double>(c->d_bwork, c->n_bwork, c->d_descs, par, c->stream);
+        }
+    }
+    lbm_status st = check_launch();
+    c->steps += nsteps;
+    return st;
+}
+
+lbm_status lbm_sync(lbm_ctx* c) {
+    if (!c) return fail(LBM_EINVAL, "null ctx");
+    if (c->sticky != LBM_OK) return fail(c->sticky, "context is unstable");
+    return read_status(c);
+}
+
+lbm_status lbm_macros_device(lbm_ctx* c, double* rho, double* ux, double* uy, double* T, double* p) {
+    if (!c || !c->eos_set) return fail(LBM_EINVAL, "context not initialised");
+    const long long nn = (long long)c->cfg.nx * c->cfg.ny;
+    if (is_fp32(c)) k_macros<float><<<grid_for(nn), 256, 0, c->stream>>>(c->d_desc, cur_buf(c), rho, ux, uy, T, p);
+    else k_macros<double><<<grid_for(nn), 256, 0, c->stream>>>(c->d_desc, cur_buf(c), rho, ux, uy, T, p);
+    return check_launch();
+}
+
+lbm_status lbm_macros(lbm_ctx* c, double* rho, double* ux, double* uy, double* T, double* p) {
+    if (!c || !c->eos_set) return fail(LBM_EINVAL, "context not initialised");
+    const long long nn = (long long)c->cfg.nx * c->cfg.ny;
+    double* host[5] = {rho, ux, uy, T, p};
+    double* dev[5];
+    for (int i = 0; i < 5; ++i) dev[i] = host[i] ? c->d_stage + i * nn : nullptr;
+    lbm_status st = lbm_macros_device(c, dev[0], dev[1], dev[2], dev[3], dev[4]);
+    if (st != LBM_OK) return st;
+    for (int i = 0; i < 5; ++i)
+        if (host[i]) CUDA_TRY(cudaMemcpyAsync(host[i], dev[i], nn * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    st = read_status(c);
+    if (st != LBM_OK) return st;
+    return c->sticky;
+}
+
+lbm_status lbm_get_state(lbm_ctx* c, double* f, double* g) {
+    if (!c || !c->eos_set) return fail(LBM_EINVAL, "context not initialised");
+    const long long nn = (long long)c->cfg.nx * c->cfg.ny;
+    for (int q = 0; q < 18; ++q) {
+        double* host = q < 9 ? (f ? f + q * nn : nullptr) : (g ? g + (q - 9) * nn : nullptr);
+        if (!host) continue;
+        const double rest = q < 9 ? c->f_rest[q] : c->g_rest[q - 9];
+        if (is_fp32(c)) k_get_plane<float><<<grid_for(nn), 256, 0, c->stream>>>(c->d_desc, cur_buf(c), q, rest, c->d_stage);
+        else k_get_plane<double><<<grid_for(nn), 256, 0, c->stream>>>(c->d_desc, cur_buf(c), q, rest, c->d_stage);
+        lbm_status st = check_launch();
+        if (st != LBM_OK) return st;
+        CUDA_TRY(cudaMemcpyAsync(host, c->d_stage, nn * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_state(lbm_ctx* c, const double* f, const double* g) {
+    if (!c || !c->eos_set || !f || !g) return fail(LBM_EINVAL, "context not initialised or null state");
+    const long long nn = (long long)c->cfg.nx * c->cfg.ny;
+    for (int q = 0; q < 18; ++q) {
+        const double* host = q < 9 ? f + q * nn : g + (q - 9) * nn;
+        const double rest = q < 9 ? c->f_rest[q] : c->g_rest[q - 9];
+        CUDA_TRY(cudaMemcpyAsync(c->d_stage, host, nn * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        if (is_fp32(c)) k_set_plane<float><<<grid_for(nn), 256, 0, c->stream>>>(c->d_desc, cur_buf(c), q, rest, c->d_stage);
+        else k_set_plane<double><<<grid_for(nn), 256, 0, c->stream>>>(c->d_desc, cur_buf(c), q, rest, c->d_stage);
+        lbm_status st = check_launch();
+        if (st != LBM_OK) return st;
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+    }
+    CUDA_TRY(cudaMemsetAsync(c->d_status, 0, 256, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->sticky = LBM_OK;
+    c->have_snap = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_init_macros(lbm_ctx* c, const double* rho, const double* ux, const double* uy, const double* T) {
+    if (!c || !c->eos_set || !rho || !ux || !uy || !T) return fail(LBM_EINVAL, "context not initialised or null field");
+    const long long nn = (long long)c->cfg.nx * c->cfg.ny;
+    const double* in[4] = {rho, ux, uy, T};
+    for (int i = 0; i < 4; ++i)
+        CUDA_TRY(cudaMemcpyAsync(c->d_stage + i * nn, in[i], nn * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if (is_fp32(c))
+        k_init_macros<float><<<grid_for(nn), 256, 0, c->stream>>>(c->d_desc, cur_buf(c), c->d_stage, c->d_stage + nn,
+                                                                 c->d_stage + 2 * nn, c->d_stage + 3 * nn);
+    else
+        k_init_macros<double><<<grid_for(nn), 256, 0, c->stream>>>(c->d_desc, cur_buf(c), c->d_stage, c->d_stage + nn,
+                                                                  c->d_stage + 2 * nn, c->d_stage + 3 * nn);
+    lbm_status st = check_launch();
+    if (st != LBM_OK) return st;
+    CUDA_TRY(cudaMemsetAsync(c->d_status, 0, 256, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->sticky = LBM_OK;
+    c->have_snap = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_nusselt(lbm_ctx* c, int wall, double* nu) {
+    if (!c || !c->eos_set || !nu || wall < 0 || wall > 3) return fail(LBM_EINVAL, "bad arguments");
+    const lbm_config& k = c->cfg;
+    if (k.wall[wall].periodic) return fail(LBM_EINVAL, "periodic side has no wall");
+    double tmax = -1e300, tmin = 1e300;
+    int nd = 0;
+    for (int s = 0; s < 4; ++s)
+        if (!k.wall[s].periodic && k.wall[s].thermal == 0) {
+            ++nd;
+            tmax = std::max(tmax, k.wall[s].T);
+            tmin = std::min(tmin, k.wall[s].T);
+        }
+    if (nd < 2 || !(tmax > tmin)) return fail(LBM_EINVAL, "Nusselt number needs two Dirichlet walls at different T");
+    if (is_fp32(c)) k_nusselt<float><<<1, 1024, 0, c->stream>>>(c->d_desc, cur_buf(c), wall, tmax - tmin, c->d_diag + 12);
+    else k_nusselt<double><<<1, 1024, 0, c->stream>>>(c->d_desc, cur_buf(c), wall, tmax - tmin, c->d_diag + 12);
+    lbm_status st = check_launch();
+    if (st != LBM_OK) return st;
+    CUDA_TRY(cudaMemcpyAsync(nu, c->d_diag + 12, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return read_status(c);
+}
+
+lbm_status lbm_diagnostics(lbm_ctx* c, int snapshot, double* out8) {
+    if (!c || !c->eos_set || !out8) return fail(LBM_EINVAL, "bad arguments");
+    const int have = c->have_snap ? 1 : 0;
+    if (is_fp32(c))
+        k_diag<float><<<kDiagBlocks, kDiagThreads, 0, c->stream>>>(c->d_desc, cur_buf(c), c->d_snap, snapshot, have, c->d_partials);
+    else
+        k_diag<double><<<kDiagBlocks, kDiagThreads, 0, c->stream>>>(c->d_desc, cur_buf(c), c->d_snap, snapshot, have, c->d_partials);
+    k_diag_final<<<1, 32, 0, c->stream>>>(c->d_partials, kDiagBlocks, c->d_diag);
+    lbm_status st = check_launch();
+    if (st != LBM_OK) return st;
+    double acc[kDiagSlots];
+    CUDA_TRY(cudaMemcpyAsync(acc, c->d_diag, sizeof(acc), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    const double nn = (double)c->cfg.nx * c->cfg.ny;
+    const Params<double>& P = c->h.pd;
+    out8[0] = nn * P.rho0 + acc[0];
+    out8[1] = nn * P.rho0 * P.E0 + acc[1];
+    out8[2] = acc[2];
+    double r = 0.0;
+    if (have) {
+        const double ru = acc[4] > 0 ? std::sqrt(acc[3] / acc[4]) : 0.0;
+        const double rT = acc[6] > 0 ? std::sqrt(acc[5] / acc[6]) : 0.0;
+        r = std::max(ru, rT);
+    }
+    out8[3] = r;
+    out8[4] = acc[7];
+    out8[5] = acc[8];
+    out8[6] = acc[9] / nn;
+    out8[7] = (double)c->steps;
+    if (snapshot) c->have_snap = true;
+    if (acc[7] > 0) {
+        c->sticky = LBM_EUNSTABLE;
+        return fail(LBM_EUNSTABLE, "non-finite nodes in the state");
+    }
+    return read_status(c);
+}
+
+// ------------------------------------------------------------------------
+// batched stepping
+// ------------------------------------------------------------------------
+
+static void batch_launch_step(lbm_batch* b, int par) {
+    for (int pr = 0; pr < 2; ++pr)
+        for (int bi = 0; bi < 2; ++bi) {
+            const int bx = bi ? 128 : 64;
+            if (!b->w_cnt[pr][bi]) continue;
+            if (pr) launch_collide<float>(b->d_work + b->w_off[pr][bi], b->w_cnt[pr][bi], bx, b->d_descs, par, b->stream);
+            else launch_collide<double>(b->d_work + b->w_off[pr][bi], b->w_cnt[pr][bi], bx, b->d_descs, par, b->stream);
+        }
+    for (int pr = 0; pr < 2; ++pr) {
+        if (!b->b_cnt[pr]) continue;
+        if (pr) launch_boundary<float>(b->d_bwork + b->b_off[pr], b->b_cnt[pr], b->d_descs, par, b->stream);
+        else launch_boundary<double>(b->d_bwork + b->b_off[pr], b->b_cnt[pr], b->d_descs, par, b->stream);
+    }
+}
+
+lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, int graph_steps, lbm_batch** out) {
+    if (!out || !ctxs || n < 1) return fail(LBM_EINVAL, "bad batch arguments");
+    *out = nullptr;
+    if (graph_steps < 0 || (graph_steps & 1)) return fail(LBM_EINVAL, "graph_steps must be even and >= 0");
+    lbm_batch* b = new lbm_batch();
+    b->stream = ctxs[0]->stream;
+    std::vector<InstDesc*> descs;
+    std::vector<Work> groups[2][2];
+    std::vector<BWork> bgroups[2];
+    for (int i = 0; i < n; ++i) {
+        lbm_ctx* c = ctxs[i];
+        if (!c || !c->eos_set || c->stream != b->stream || c->sticky != LBM_OK) {
+            delete b;
+            return fail(LBM_EINVAL, "batch members must be initialised, stable and share one stream");
+        }
+        b->ctxs.push_back(c);
+        descs.push_back(c->d_desc);
+        const int pr = is_fp32(c) ? 1 : 0, bi = c->bx == 128 ? 1 : 0;
+        const int par = (int)(c->steps & 1);
+        auto w = make_work(c->cfg, i, c->bx, c->by, par);
+        groups[pr][bi].insert(groups[pr][bi].end(), w.begin(), w.end());
+        auto bw = make_bwork(c->cfg, i, par);
+        bgroups[pr].insert(bgroups[pr].end(), bw.begin(), bw.end());
+    }
+    std::vector<Work> all;
+    for (int pr = 0; pr < 2; ++pr)
+        for (int bi = 0; bi < 2; ++bi) {
+            b->w_off[pr][bi] = (int)all.size();
+            b->w_cnt[pr][bi] = (int)groups[pr][bi].size();
+            all.insert(all.end(), groups[pr][bi].begin(), groups[pr][bi].end());
+        }
+    std::vector<BWork> ball;
+    for (int pr = 0; pr < 2; ++pr) {
+        b->b_off[pr] = (int)ball.size();
+        b->b_cnt[pr] = (int)bgroups[pr].size();
+        ball.insert(ball.end(), bgroups[pr].begin(), bgroups[pr].end());
+    }
+    auto bad = [&](const char* m) {
+        lbm_batch_destroy(b);
+        return fail(LBM_ECUDA, m);
+    };
+    if (cudaMalloc(&b->d_descs, descs.size() * sizeof(InstDesc*)) != cudaSuccess) return bad("cudaMalloc descs");
+    if (!all.empty() && cudaMalloc(&b->d_work, all.size() * sizeof(Work)) != cudaSuccess) return bad("cudaMalloc work");
+    if (!ball.empty() && cudaMalloc(&b->d_bwork, ball.size() * sizeof(BWork)) != cudaSuccess) return bad("cudaMalloc bwork");
+    if (cudaMemcpyAsync(b->d_descs, descs.data(), descs.size() * sizeof(InstDesc*), cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+        return bad("upload descs");
+    if (!all.empty() && cudaMemcpyAsync(b->d_work, all.data(), all.size() * sizeof(Work), cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+        return bad("upload work");
+    if (!ball.empty() && cudaMemcpyAsync(b->d_bwork, ball.data(), ball.size() * sizeof(BWork), cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+        return bad("upload bwork");
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bad("sync");
+    b->graph_steps = graph_steps;
+    if (graph_steps > 0) {
+        if (!b->stream) {
+            lbm_batch_destroy(b);
+            return fail(LBM_EINVAL, "graph capture needs a non-default stream");
+        }
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return bad("begin capture");
+        for (int s = 0; s < graph_steps; ++s) batch_launch_step(b, s & 1);
+        if (cudaStreamEndCapture(b->stream, &g) != cudaSuccess) return bad("end capture");
+        cudaError_t e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return bad("graph instantiate");
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_batch* b, long nsteps) {
+    if (!b || nsteps < 0) return fail(LBM_EINVAL, "bad batch step");
+    for (lbm_ctx* c : b->ctxs)
+        if (c->sticky != LBM_OK) return fail(c->sticky, "a batch member is unstable");
+    if (b->graph) {
+        if (nsteps % b->graph_steps) return fail(LBM_EINVAL, "nsteps must be a multiple of graph_steps");
+        for (long s = 0; s < nsteps; s += b->graph_steps) CUDA_TRY(cudaGraphLaunch(b->graph, b->stream));
+    } else {
+        for (long s = 0; s < nsteps; ++s) batch_launch_step(b, (int)((b->steps + s) & 1));
+        lbm_status st = check_launch();
+        if (st != LBM_OK) return st;
+    }
+    b->steps += nsteps;
+    for (lbm_ctx* c : b->ctxs) c->steps += nsteps;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_step_profiled(lbm_batch* b, long nsteps, double* ms_collide, double* ms_wall) {
+    if (!b || nsteps < 1 || nsteps > 100000 || !ms_collide || !ms_wall) return fail(LBM_EINVAL, "bad profiled step");
+    for (lbm_ctx* c : b->ctxs)
+        if (c->sticky != LBM_OK) return fail(c->sticky, "a batch member is unstable");
+    std::vector<cudaEvent_t> ev((size_t)3 * nsteps, nullptr);
+    auto cleanup = [&]() {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+    };
+    for (auto& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) { cleanup(); return fail(LBM_ECUDA, "cudaEventCreate"); }
+    for (long s = 0; s < nsteps; ++s) {
+        const int par = (int)((b->steps + s) & 1);
+        cudaEventRecord(ev[3 * s], b->stream);
+        for (int pr = 0; pr < 2; ++pr)
+            for (int bi = 0; bi < 2; ++bi) {
+                if (!b->w_cnt[pr][bi]) continue;
+                const int bx = bi ? 128 : 64;
+                if (pr) launch_collide<float>(b->d_work + b->w_off[pr][bi], b->w_cnt[pr][bi], bx, b->d_descs, par, b->stream);
+                else launch_collide<double>(b->d_work + b->w_off[pr][bi], b->w_cnt[pr][bi], bx, b->d_descs, par, b->stream);
+            }
+        cudaEventRecord(ev[3 * s + 1], b->stream);
+        for (int pr = 0; pr < 2; ++pr) {
+            if (!b->b_cnt[pr]) continue;
+            if (pr) launch_boundary<float>(b->d_bwork + b->b_off[pr], b->b_cnt[pr], b->d_descs, par, b->stream);
+            else launch_boundary<double>(b->d_bwork + b->b_off[pr], b->b_cnt[pr], b->d_descs, par, b->stream);
+        }
+        cudaEventRecord(ev[3 * s + 2], b->stream);
+    }
+    lbm_status st = check_launch();
+    if (st != LBM_OK) { cleanup(); return st; }
+    if (cudaEventSynchronize(ev[3 * nsteps - 1]) != cudaSuccess) { cleanup(); return fail(LBM_ECUDA, "event sync"); }
+    double tc = 0.0, tw = 0.0;
+    for (long s = 0; s < nsteps; ++s) {
+        float a = 0.f, c2 = 0.f;
+        cudaEventElapsedTime(&a, ev[3 * s], ev[3 * s + 1]);
+        cudaEventElapsedTime(&c2, ev[3 * s + 1], ev[3 * s + 2]);
+        tc += a;
+        tw += c2;
+    }
+    cleanup();
+    *ms_collide = tc;
+    *ms_wall = tw;
+    b->steps += nsteps;
+    for (lbm_ctx* c : b->ctxs) c->steps += nsteps;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_destroy(lbm_batch* b) {
+    if (!b) return LBM_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    else cudaDeviceSynchronize();
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->d_descs) cudaFree(b->d_descs);
+    if (b->d_work) cudaFree(b->d_work);
+    if (b->d_bwork) cudaFree(b->d_bwork);
+    delete b;
+    return LBM_OK;
+}
+
+}  // extern "C"
