@@ -240,6 +240,8 @@ def main():
         ev1.synchronize()
         barrier()
     ms = ev0.elapsed_time(ev1)
+    for lat in lats:        # a run that produced NaN/Inf is not a measurement
+        lat.sync()
     if world > 1:
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)

@@ -1,0 +1,102 @@
+"""Launch-shape autotuner for the fused collide-stream kernel.
+
+The fused kernel gives each CTA a strip of ``bx`` columns (64 or 128
+threads) and a run of ``by`` rows that it sweeps with a three-row ring of
+rho' and p' in shared memory.  Short runs give more CTAs (better SM fill on
+small lattices) but re-read two halo rows per run; long runs amortise the
+halo but may leave SMs idle.  The best shape depends on the lattice shape and
+the precision, so it is measured: every candidate is timed with CUDA events
+on the lattice's own stream, and the winner is cached per
+(precision, nx class, ny class) in a JSON file.
+"""
+from __future__ import annotations
+
+import json
+import os
+import threading
+
+from . import lbm
+
+_CACHE_PATH = os.environ.get(
+    "LBM_TUNE_CACHE", os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tile_cache.json"))
+_lock = threading.Lock()
+BX_CANDIDATES = (64, 128)
+BY_CANDIDATES = (4, 8, 16, 32, 64, 128)
+
+
+def size_class(n: int) -> int:
+    """Round a lattice extent up to the next power of two (>= 16)."""
+    c = 16
+    while c < n:
+        c *= 2
+    return c
+
+
+def key_for(cfg: dict) -> str:
+    return f"p{int(cfg.get('precision', 0))}_x{size_class(cfg['nx'])}_y{size_class(cfg['ny'])}"
+
+
+def _load():
+    try:
+        with open(_CACHE_PATH) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+def _store(d):
+    os.makedirs(os.path.dirname(_CACHE_PATH), exist_ok=True)
+    tmp = _CACHE_PATH + f".tmp{os.getpid()}"
+    with open(tmp, "w") as fh:
+        json.dump(d, fh, indent=1, sort_keys=True)
+    os.replace(tmp, _CACHE_PATH)
+
+
+def candidates(cfg: dict):
+    out = []
+    for bx in BX_CANDIDATES:
+        if bx == 128 and cfg["nx"] <= 64:
+            continue
+        for by in BY_CANDIDATES:
+            if by > cfg["ny"] and by != BY_CANDIDATES[0]:
+                continue
+            out.append((bx, by))
+    return out
+
+
+def measure(cfg: dict, bx: int, by: int, steps: int = 20, stream=None) -> float:
+    """MLUPS of the fused kernel alone for one launch shape."""
+    lat = lbm.Lattice(cfg, stream=stream)
+    lat.set_tile(bx, by)
+    batch = lbm.Batch([lat], graph_steps=0)
+    batch.step_profiled(4)                       # warm-up
+    ms, _ = batch.step_profiled(steps)
+    batch.close()
+    lat.close()
+    return cfg["nx"] * cfg["ny"] * steps / (ms * 1e-3) / 1e6
+
+
+def tune(cfg: dict, steps: int = 20, force: bool = False, stream=None) -> tuple:
+    """Best (bx, by) for this configuration's class, measured on first use."""
+    key = key_for(cfg)
+    with _lock:
+        cache = _load()
+        if key in cache and not force:
+            return tuple(cache[key]["tile"])
+    results = {}
+    for bx, by in candidates(cfg):
+        results[(bx, by)] = measure(cfg, bx, by, steps, stream)
+    best = max(results, key=results.get)
+    with _lock:
+        cache = _load()
+        cache[key] = {"tile": list(best), "mlups": results[best],
+                      "all": {f"{b[0]}x{b[1]}": v for b, v in results.items()}}
+        _store(cache)
+    return best
+
+
+def apply(lattices, steps: int = 20):
+    """Set every lattice's launch shape from the cache, tuning unseen classes."""
+    for lat in lattices:
+        bx, by = tune(lat.cfg, steps=steps, stream=lat.stream)
+        lat.set_tile(bx, by)

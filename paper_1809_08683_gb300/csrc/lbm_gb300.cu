@@ -57,7 +57,8 @@ struct InstDesc {
 };
 
 struct Work {  // one CTA of the fused kernel
-    int inst, x0, y0, y1, par, pad0, pad1, pad2;
+    int inst, x0, y0, y1, par, pad0;
+    long long step0;  // the lattice's step count when this table was built
 };
 
 struct BWork {  // one CTA of the wall pass
@@ -99,6 +100,33 @@ __device__ void load_params(Params<R>* dst, const Params<R>* src) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = s[i];
 }
 
+// Unbiased (stochastic) rounding of FP32 stores.  With round-to-nearest a
+// nearly steady state repeats the same rounding error every step, which acts
+// like a spurious body force of up to ulp(f')/2 per step; adding uniform noise
+// of one ulp of the stored value before rounding makes the expected stored
+// value equal the exact one.  The noise comes from a counter-based hash of
+// (node, absolute step), so a lattice gives the same bits alone or batched.
+__device__ __forceinline__ uint32_t mix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x7feb352du;
+    h ^= h >> 15;
+    h *= 0x846ca68bu;
+    h ^= h >> 16;
+    return h;
+}
+
+struct AddDither {
+    mutable uint32_t h;
+    __device__ __forceinline__ float operator()(float old, float delta) const {
+        h = h * 1664525u + 1013904223u;                       // one LCG step per store
+        const float r = (float)(int)h * 2.3283064365386963e-10f;  // uniform in [-1/2, 1/2)
+        const int e = (__float_as_int(old) & 0x7f800000) - (23 << 23);
+        const float ulp = __int_as_float(e > 0 ? e : 0);
+        return old + fmaf(r, ulp, delta);
+    }
+    __device__ __forceinline__ double operator()(double old, double delta) const { return old + delta; }
+};
+
 // rho' and p' of node (xx, yy) read straight from a buffer.
 template <typename R>
 __device__ void rho_p_at(const Params<R>& P, const R* __restrict__ src, long long plane, int pitch,
@@ -112,27 +140,115 @@ __device__ void rho_p_at(const Params<R>& P, const R* __restrict__ src, long lon
 }
 
 // ------------------------------------------------------------------------
+// TMA bulk copies and mbarriers (inline PTX, sm_90+ forms valid on sm_103a)
+// ------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after about 2^32 SM cycles (2 s at 2 GHz).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > (1LL << 32)) return false;
+    return true;
+}
+
+// Global -> shared bulk copy completing on an mbarrier; addresses 16-byte
+// aligned, size a multiple of 16 bytes.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// ------------------------------------------------------------------------
 // fused collide + stream
 // ------------------------------------------------------------------------
 
-template <typename R, int BX>
+// Shared-memory layout of the fused kernel: S stages of one lattice row of
+// the CTA's strip (18 planes, each [16-byte left-halo chunk][BX][16-byte
+// right-halo chunk]), one mbarrier per stage, the parameters, and a 4-row
+// ring of rho' and p' over the strip plus its two halo columns.
+template <typename R, int BX, int S>
+struct FusedSmem {
+    static constexpr int E = 16 / (int)sizeof(R);  // elements per 16-byte chunk
+    static constexpr int W = BX + 2 * E;            // stage row width per plane
+    static constexpr size_t stage_bytes = (size_t)18 * W * sizeof(R);
+    static constexpr size_t off_bars = (size_t)S * stage_bytes;
+    static constexpr size_t off_params = off_bars + 8 * S;
+    static constexpr size_t off_ring = (off_params + sizeof(Params<R>) + 15) / 16 * 16;
+    static constexpr size_t bytes = off_ring + (size_t)2 * 4 * (BX + 2) * sizeof(R);
+};
+
+template <typename R, int BX, int S>
 __global__ void __launch_bounds__(BX) k_collide_stream(const Work* __restrict__ work,
-                                                       InstDesc* const* __restrict__ descs, int step_par) {
-    __shared__ Params<R> P;
-    __shared__ R s_rho[3][BX + 2];
-    __shared__ R s_p[3][BX + 2];
+                                                       InstDesc* const* __restrict__ descs, int step_par,
+                                                       const long long* __restrict__ counter) {
+    using L = FusedSmem<R, BX, S>;
+    constexpr int E = L::E, W = L::W;
+    extern __shared__ __align__(128) unsigned char smem[];
+    R* stage = reinterpret_cast<R*>(smem);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::off_bars);
+    Params<R>& P = *reinterpret_cast<Params<R>*>(smem + L::off_params);
+    R(*s_rho)[BX + 2] = reinterpret_cast<R(*)[BX + 2]>(smem + L::off_ring);
+    R(*s_p)[BX + 2] = s_rho + 4;
+    __shared__ int s_abort;
+
     const Work w = work[blockIdx.x];
     const InstDesc* D = descs[w.inst];
     load_params(&P, &dparams<R>(D));
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int k = 0; k < S; ++k) mbar_init(&bars[k], 1);
+        fence_mbar_init();
+        s_abort = 0;
+    }
     const int nx = D->nx, ny = D->ny, pitch = D->pitch, px = D->px, py = D->py;
     const long long plane = D->plane;
     const int b = w.par ^ step_par;
     const R* __restrict__ src = reinterpret_cast<const R*>(D->buf[b]);
     R* __restrict__ dst = reinterpret_cast<R*>(D->buf[b ^ 1]);
     unsigned int* status = D->status;
+    const uint32_t step_hash = mix32((uint32_t)(w.step0 + *counter) * 0x9e3779b1u + 0x632be5abu);
     __syncthreads();
 
-    const int tid = threadIdx.x;
     const int x = w.x0 + tid;
     const bool active = x < nx;
     const int xlast = min(w.x0 + BX, nx) - 1;
@@ -143,51 +259,98 @@ __global__ void __launch_bounds__(BX) k_collide_stream(const Work* __restrict__ 
     int xhr = xlast + 1;
     bool has_r = true;
     if (xhr >= nx) { if (px) xhr = 0; else has_r = false; }
+    const int xcl = has_l ? (xhl / E) * E : 0, xcr = has_r ? (xhr / E) * E : 0;
+    const int nmain = min(BX, pitch - w.x0);  // multiple of 32 elements: 16-byte sized
+    const int nrows = w.y1 - w.y0;
+    const int last_l = nrows + 1;             // logical rows 0..last_l = physical y0-1..y1
     const int c = tid + 1;
 
-    // macros of one row into a ring slot; active threads keep their DFs in v
-    auto row_macros = [&](int yy, int slot, R* v, Mac<R>& m) {
+    // physical row of logical row l, or -1 if it lies outside a walled lattice
+    auto phys = [&](int l) -> int {
+        int y = w.y0 - 1 + l;
+        if (y < 0 || y >= ny) {
+            if (!py) return -1;
+            y = (y < 0) ? y + ny : y - ny;
+        }
+        return y;
+    };
+
+    // warp 0 issues the copies of logical row l into stage l % S; a row that
+    // does not exist still completes its barrier phase (plain arrive)
+    auto issue = [&](int l) {
+        if (l > last_l || tid >= 32) return;
+        const int s = l % S;
+        const int y = phys(l);
+        if (tid == 0) {
+            if (y < 0) mbar_arrive(&bars[s]);
+            else mbar_arrive_expect_tx(&bars[s], (uint32_t)(18 * (nmain * (int)sizeof(R) + 16 * (has_l + has_r))));
+        }
+        __syncwarp();
+        if (y >= 0 && tid < 18) {
+            fence_proxy_async();
+            const R* row = src + tid * plane + (long long)y * pitch;
+            R* st = stage + (size_t)s * 18 * W + (size_t)tid * W;
+            bulk_g2s(st + E, row + w.x0, (uint32_t)(nmain * sizeof(R)), &bars[s]);
+            if (has_l) bulk_g2s(st, row + xcl, 16u, &bars[s]);
+            if (has_r) bulk_g2s(st + E + BX, row + xcr, 16u, &bars[s]);
+        }
+    };
+
+    // wait for logical row l and put its rho', p' into ring slot l % 4;
+    // active threads also return their own node's macros in m
+    auto row_macros = [&](int l, Mac<R>& m) -> bool {
+        const int s = l % S;
+        if (!mbar_wait(&bars[s], (uint32_t)((l / S) & 1))) {
+            atomicOr(status, 2u);
+            s_abort = 1;
+            return false;
+        }
+        const R* st = stage + (size_t)s * 18 * W;
+        const int slot = l & 3;
         if (active) {
-            load18(src, plane, (long long)yy * pitch + x, v);
+            R v[18];
+#pragma unroll
+            for (int q = 0; q < 18; ++q) v[q] = st[q * W + E + tid];
             node_macros(P, v, m);
             s_rho[slot][c] = m.rho_d;
             s_p[slot][c] = m.p_d;
         }
         if (tid == 0 && has_l) {
-            R rd, pd;
-            rho_p_at(P, src, plane, pitch, xhl, yy, rd, pd);
-            s_rho[slot][0] = rd;
-            s_p[slot][0] = pd;
+            R v[18];
+#pragma unroll
+            for (int q = 0; q < 18; ++q) v[q] = st[q * W + (xhl - xcl)];
+            Mac<R> h;
+            node_macros(P, v, h);
+            s_rho[slot][0] = h.rho_d;
+            s_p[slot][0] = h.p_d;
         }
         if (tid == tlast && has_r) {
-            R rd, pd;
-            rho_p_at(P, src, plane, pitch, xhr, yy, rd, pd);
-            s_rho[slot][tlast + 2] = rd;
-            s_p[slot][tlast + 2] = pd;
+            R v[18];
+#pragma unroll
+            for (int q = 0; q < 18; ++q) v[q] = st[q * W + E + BX + (xhr - xcr)];
+            Mac<R> h;
+            node_macros(P, v, h);
+            s_rho[slot][tlast + 2] = h.rho_d;
+            s_p[slot][tlast + 2] = h.p_d;
         }
+        return true;
     };
 
-    R cur[18], nxt[18];
+    for (int l = 0; l < S; ++l) issue(l);
     Mac<R> mc, mn;
-    {
-        int ym = w.y0 - 1;
-        bool has_m = true;
-        if (ym < 0) { if (py) ym = ny - 1; else has_m = false; }
-        if (has_m) row_macros(ym, 0, nxt, mn);
-        row_macros(w.y0, 1, cur, mc);
-    }
+    if (phys(0) >= 0) row_macros(0, mn);
+    row_macros(1, mc);
 
-    for (int j = w.y0; j < w.y1; ++j) {
-        const int jl = j - w.y0;
-        const int sm = jl % 3, s0 = (jl + 1) % 3, sp = (jl + 2) % 3;
-        int yn = j + 1;
-        bool has_n = true;
-        if (yn >= ny) { if (py) yn = 0; else has_n = false; }
-        if (has_n) row_macros(yn, sp, nxt, mn);
+    for (int k = 0; k < nrows; ++k) {
+        const int j = w.y0 + k;
+        if (phys(k + 2) >= 0) row_macros(k + 2, mn);
         __syncthreads();
+        if (s_abort) break;
+        issue(k + S);  // stage of logical row k is free: its collision finished before the barrier
 
         if (active) {
             if (!(isfinite(mc.rho_d) && isfinite(mc.T_d))) atomicOr(status, 1u);
+            const int sm = k & 3, s0 = (k + 1) & 3, sp = (k + 2) & 3;
             const bool onS = !py && j == 0, onN = !py && j == ny - 1;
             const bool onW = !px && x == 0, onE = !px && x == nx - 1;
             R grx, gry, gpx, gpy;
@@ -231,33 +394,52 @@ __global__ void __launch_bounds__(BX) k_collide_stream(const Work* __restrict__ 
                 }
             }
 
-            lbm::collide(P, mc, cur, cur + 9, grx, gry, gpx, gpy);
-
-            // push; a population leaving the domain returns reversed to this node
+            R v[18];
+            const R* st = stage + (size_t)((k + 1) % S) * 18 * W + E + tid;
 #pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const int ex = (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
-                const int ey = (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
-                const int opp = (i == 0) ? 0 : (i <= 4 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5);
-                int xd = x + ex, yd = j + ey;
-                bool out = false;
-                if (xd < 0 || xd >= nx) { if (px) xd = (xd < 0) ? nx - 1 : 0; else out = true; }
-                if (yd < 0 || yd >= ny) { if (py) yd = (yd < 0) ? ny - 1 : 0; else out = true; }
-                if (out) {
-                    const long long o = (long long)j * pitch + x;
-                    dst[opp * plane + o] = cur[i];
-                    dst[(9 + opp) * plane + o] = cur[9 + i];
-                } else {
-                    const long long o = (long long)yd * pitch + xd;
-                    dst[i * plane + o] = cur[i];
-                    dst[(9 + i) * plane + o] = cur[9 + i];
+            for (int q = 0; q < 18; ++q) v[q] = st[q * W];
+            AddDither add{mix32(step_hash ^ ((uint32_t)j * 0x85ebca77u + (uint32_t)x * 0xc2b2ae3du))};
+            lbm::collide(P, mc, v, v + 9, grx, gry, gpx, gpy, add);
+
+            R* o = dst + ((long long)j * pitch + x);
+            if (x >= 1 && x <= nx - 2 && j >= 1 && j <= ny - 2) {
+                // interior: every population lands in the domain, no wrap
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const int ex = (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+                    const int ey = (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+                    const int off = ey * pitch + ex;
+                    o[i * plane + off] = v[i];
+                    o[(9 + i) * plane + off] = v[9 + i];
+                }
+            } else {
+                // edge node: periodic wrap, or bounce-back into its own slot
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const int ex = (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+                    const int ey = (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+                    const int opp = (i == 0) ? 0 : (i <= 4 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5);
+                    int xd = x + ex, yd = j + ey;
+                    bool out = false;
+                    if (xd < 0 || xd >= nx) { if (px) xd = (xd < 0) ? nx - 1 : 0; else out = true; }
+                    if (yd < 0 || yd >= ny) { if (py) yd = (yd < 0) ? ny - 1 : 0; else out = true; }
+                    if (out) {
+                        o[opp * plane] = v[i];
+                        o[(9 + opp) * plane] = v[9 + i];
+                    } else {
+                        const long long t2 = (long long)yd * pitch + xd;
+                        dst[i * plane + t2] = v[i];
+                        dst[(9 + i) * plane + t2] = v[9 + i];
+                    }
                 }
             }
         }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < 18; ++q) cur[q] = nxt[q];
         mc = mn;
+    }
+    if (s_abort && tid == 0) {
+        // leave no bulk copy in flight into this CTA's shared memory
+        for (int l = 0; l <= last_l; ++l)
+            if (phys(l) >= 0) mbar_wait(&bars[l % S], (uint32_t)((l / S) & 1));
     }
 }
 
@@ -323,9 +505,14 @@ __device__ void wall_node(const InstDesc* D, int k, WallNode& n) {
 
 template <typename R>
 __global__ void __launch_bounds__(128) k_boundary(const BWork* __restrict__ work,
-                                                  InstDesc* const* __restrict__ descs, int step_par) {
+                                                  InstDesc* const* __restrict__ descs, int step_par,
+                                                  long long* __restrict__ counter) {
     __shared__ Params<R> P;
+    // the last wall-pass launch of a step advances the step counter that the
+    // next step's fused launch reads
+    if (counter && blockIdx.x == 0 && threadIdx.x == 0) *counter += 1;
     const BWork w = work[blockIdx.x];
+    if (w.cnt <= 0) return;
     const InstDesc* D = descs[w.inst];
     load_params(&P, &dparams<R>(D));
     __syncthreads();
@@ -695,6 +882,7 @@ struct lbm_ctx {
     InstDesc* d_desc = nullptr;
     InstDesc** d_descs = nullptr;
     unsigned int* d_status = nullptr;
+    long long* d_counter = nullptr;  // absolute step read by the fused kernel
     double* d_diag = nullptr;
     double* d_partials = nullptr;
     double* d_snap = nullptr;
@@ -724,11 +912,12 @@ struct lbm_batch {
     long steps = 0;
     int graph_steps = 0;
     cudaGraphExec_t graph = nullptr;
+    long long* d_counter = nullptr;  // batch step counter, advanced on the device
 };
 
 namespace {
 
-std::vector<Work> make_work(const lbm_config& c, int inst, int bx, int by, int par) {
+std::vector<Work> make_work(const lbm_config& c, int inst, int bx, int by, int par, long long step0) {
     std::vector<Work> v;
     for (int y0 = 0; y0 < c.ny; y0 += by)
         for (int x0 = 0; x0 < c.nx; x0 += bx) {
@@ -738,6 +927,7 @@ std::vector<Work> make_work(const lbm_config& c, int inst, int bx, int by, int p
             w.y0 = y0;
             w.y1 = std::min(y0 + by, c.ny);
             w.par = par;
+            w.step0 = step0;
             v.push_back(w);
         }
     return v;
@@ -758,6 +948,17 @@ std::vector<BWork> make_bwork(const lbm_config& c, int inst, int par) {
     return v;
 }
 
+// A fully periodic lattice has no wall nodes; one empty item keeps a wall-pass
+// launch in every step so that it can advance the step counter.
+void ensure_tick(std::vector<BWork>& v, int inst, int par) {
+    if (v.empty()) {
+        BWork b{};
+        b.inst = inst;
+        b.par = par;
+        v.push_back(b);
+    }
+}
+
 int default_rows(const lbm_config& c, int bx) {
     // enough CTAs to cover 152 SMs several times, runs of at most 64 rows
     const long long strips = (c.nx + bx - 1) / bx;
@@ -768,7 +969,7 @@ int default_rows(const lbm_config& c, int bx) {
 
 lbm_status upload_work(lbm_ctx* c) {
     if (c->d_work) { cudaFree(c->d_work); c->d_work = nullptr; }
-    c->h_work = make_work(c->cfg, 0, c->bx, c->by, 0);
+    c->h_work = make_work(c->cfg, 0, c->bx, c->by, 0, 0);
     c->n_work = (int)c->h_work.size();
     CUDA_TRY(cudaMalloc(&c->d_work, c->h_work.size() * sizeof(Work)));
     CUDA_TRY(cudaMemcpyAsync(c->d_work, c->h_work.data(), c->h_work.size() * sizeof(Work),
@@ -776,17 +977,51 @@ lbm_status upload_work(lbm_ctx* c) {
     return LBM_OK;
 }
 
-template <typename R>
-void launch_collide(const Work* work, int n, int bx, InstDesc* const* descs, int par, cudaStream_t s) {
-    if (n <= 0) return;
-    if (bx == 64) k_collide_stream<R, 64><<<n, 64, 0, s>>>(work, descs, par);
-    else k_collide_stream<R, 128><<<n, 128, 0, s>>>(work, descs, par);
+constexpr int kStages = 4;
+
+template <typename R, int BX>
+cudaError_t configure_collide() {
+    cudaError_t e = cudaFuncSetAttribute(k_collide_stream<R, BX, kStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)FusedSmem<R, BX, kStages>::bytes);
+    if (e != cudaSuccess) return e;
+    // prefer shared memory over L1: the row stages, not L1, feed the kernel
+    return cudaFuncSetAttribute(k_collide_stream<R, BX, kStages>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared);
+}
+
+// Dynamic shared memory above 48 KB must be enabled per kernel before its
+// first launch (and before any graph capture that contains it).
+lbm_status configure_kernels() {
+    static int done = 0;
+    if (done) return LBM_OK;
+    cudaError_t e = configure_collide<float, 64>();
+    if (e == cudaSuccess) e = configure_collide<float, 128>();
+    if (e == cudaSuccess) e = configure_collide<double, 64>();
+    if (e == cudaSuccess) e = configure_collide<double, 128>();
+    if (e != cudaSuccess) return fail(LBM_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+    done = 1;
+    return LBM_OK;
+}
+
+template <typename R, int BX>
+void launch_collide_bx(const Work* work, int n, InstDesc* const* descs, int par, const long long* counter,
+                       cudaStream_t s) {
+    k_collide_stream<R, BX, kStages><<<n, BX, FusedSmem<R, BX, kStages>::bytes, s>>>(work, descs, par, counter);
 }
 
 template <typename R>
-void launch_boundary(const BWork* work, int n, InstDesc* const* descs, int par, cudaStream_t s) {
+void launch_collide(const Work* work, int n, int bx, InstDesc* const* descs, int par, const long long* counter,
+                    cudaStream_t s) {
     if (n <= 0) return;
-    k_boundary<R><<<n, 128, 0, s>>>(work, descs, par);
+    if (bx == 64) launch_collide_bx<R, 64>(work, n, descs, par, counter, s);
+    else launch_collide_bx<R, 128>(work, n, descs, par, counter, s);
+}
+
+template <typename R>
+void launch_boundary(const BWork* work, int n, InstDesc* const* descs, int par, long long* counter,
+                     cudaStream_t s) {
+    if (n <= 0) return;
+    k_boundary<R><<<n, 128, 0, s>>>(work, descs, par, counter);
 }
 
 int grid_for(long long nn) {
@@ -804,6 +1039,10 @@ lbm_status read_status(lbm_ctx* c) {
     unsigned int st = 0;
     CUDA_TRY(cudaMemcpyAsync(&st, c->d_status, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (st & 2u) {
+        c->sticky = LBM_ETIMEOUT;
+        return fail(LBM_ETIMEOUT, "a bounded wait on a bulk copy gave up");
+    }
     if (st & 1u) {
         c->sticky = LBM_EUNSTABLE;
         return fail(LBM_EUNSTABLE, "non-finite density or temperature detected");
@@ -835,6 +1074,7 @@ lbm_status lbm_create(const lbm_config* cfg, void* workspace, size_t workspace_b
     *out = nullptr;
     lbm_status st = validate(cfg);
     if (st != LBM_OK) return st;
+    if ((st = configure_kernels()) != LBM_OK) return st;
     lbm_ctx* c = new lbm_ctx();
     c->cfg = *cfg;
     c->stream = (cudaStream_t)cuda_stream;
@@ -858,6 +1098,7 @@ lbm_status lbm_create(const lbm_config* cfg, void* workspace, size_t workspace_b
     c->d_desc = (InstDesc*)(c->ws + c->L.off_desc);
     c->d_descs = (InstDesc**)(c->ws + c->L.off_descs);
     c->d_status = (unsigned int*)(c->ws + c->L.off_status);
+    c->d_counter = (long long*)(c->ws + c->L.off_status + 128);
     c->d_diag = (double*)(c->ws + c->L.off_diag);
     c->d_partials = (double*)(c->ws + c->L.off_partials);
     c->d_snap = (double*)(c->ws + c->L.off_snap);
@@ -893,6 +1134,7 @@ lbm_status lbm_create(const lbm_config* cfg, void* workspace, size_t workspace_b
     c->by = default_rows(*cfg, c->bx);
     if ((st = upload_work(c)) != LBM_OK) return cleanup(st);
     c->h_bwork = make_bwork(*cfg, 0, 0);
+    ensure_tick(c->h_bwork, 0, 0);
     c->n_bwork = (int)c->h_bwork.size();
     if (c->n_bwork) {
         if (cudaMalloc(&c->d_bwork, c->h_bwork.size() * sizeof(BWork)) != cudaSuccess)
@@ -1059,14 +1301,17 @@ lbm_status lbm_step(lbm_ctx* c, long nsteps) {
     if (!c || !c->eos_set) return fail(LBM_EINVAL, "context not initialised");
     if (nsteps < 0) return fail(LBM_EINVAL, "nsteps < 0");
     if (c->sticky != LBM_OK) return fail(c->sticky, "context is unstable");
+    if (nsteps == 0) return LBM_OK;
+    const long long base = c->steps;
+    CUDA_TRY(cudaMemcpyAsync(c->d_counter, &base, sizeof(base), cudaMemcpyHostToDevice, c->stream));
     for (long s = 0; s < nsteps; ++s) {
         const int par = (int)((c->steps + s) & 1);
         if (is_fp32(c)) {
-            launch_collide<float>(c->d_work, c->n_work, c->bx, c->d_descs, par, c->stream);
-            launch_boundary<float>(c->d_bwork, c->n_bwork, c->d_descs, par, c->stream);
+            launch_collide<float>(c->d_work, c->n_work, c->bx, c->d_descs, par, c->d_counter, c->stream);
+            launch_boundary<float>(c->d_bwork, c->n_bwork, c->d_descs, par, c->d_counter, c->stream);
         } else {
-            launch_collide<double>(c->d_work, c->n_work, c->bx, c->d_descs, par, c->stream);
-            launch_boundary<double>(c->d_bwork, c->n_bwork, c->d_descs, par, c->stream);
+            launch_collide<double>(c->d_work, c->n_work, c->bx, c->d_descs, par, c->d_counter, c->stream);
+            launch_boundary<double>(c->d_bwork, c->n_bwork, c->d_descs, par, c->d_counter, c->stream);
         }
     }
     lbm_status st = check_launch();
@@ -1223,19 +1468,37 @@ lbm_status lbm_diagnostics(lbm_ctx* c, int snapshot, double* out8) {
 // batched stepping
 // ------------------------------------------------------------------------
 
-static void batch_launch_step(lbm_batch* b, int par) {
+static void batch_launch_collide(lbm_batch* b, int par) {
     for (int pr = 0; pr < 2; ++pr)
         for (int bi = 0; bi < 2; ++bi) {
             const int bx = bi ? 128 : 64;
             if (!b->w_cnt[pr][bi]) continue;
-            if (pr) launch_collide<float>(b->d_work + b->w_off[pr][bi], b->w_cnt[pr][bi], bx, b->d_descs, par, b->stream);
-            else launch_collide<double>(b->d_work + b->w_off[pr][bi], b->w_cnt[pr][bi], bx, b->d_descs, par, b->stream);
+            if (pr)
+                launch_collide<float>(b->d_work + b->w_off[pr][bi], b->w_cnt[pr][bi], bx, b->d_descs, par, b->d_counter, b->stream);
+            else
+                launch_collide<double>(b->d_work + b->w_off[pr][bi], b->w_cnt[pr][bi], bx, b->d_descs, par, b->d_counter, b->stream);
         }
+}
+
+static void batch_launch_boundary(lbm_batch* b, int par) {
+    const int last = b->b_cnt[1] ? 1 : 0;
     for (int pr = 0; pr < 2; ++pr) {
         if (!b->b_cnt[pr]) continue;
-        if (pr) launch_boundary<float>(b->d_bwork + b->b_off[pr], b->b_cnt[pr], b->d_descs, par, b->stream);
-        else launch_boundary<double>(b->d_bwork + b->b_off[pr], b->b_cnt[pr], b->d_descs, par, b->stream);
+        long long* ctr = (pr == last) ? b->d_counter : nullptr;
+        if (pr) launch_boundary<float>(b->d_bwork + b->b_off[pr], b->b_cnt[pr], b->d_descs, par, ctr, b->stream);
+        else launch_boundary<double>(b->d_bwork + b->b_off[pr], b->b_cnt[pr], b->d_descs, par, ctr, b->stream);
     }
+}
+
+static void batch_launch_step(lbm_batch* b, int par) {
+    batch_launch_collide(b, par);
+    batch_launch_boundary(b, par);
+}
+
+static lbm_status batch_set_counter(lbm_batch* b) {
+    const long long v = b->steps;
+    CUDA_TRY(cudaMemcpyAsync(b->d_counter, &v, sizeof(v), cudaMemcpyHostToDevice, b->stream));
+    return LBM_OK;
 }
 
 lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, int graph_steps, lbm_batch** out) {
@@ -1257,7 +1520,7 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, int graph_steps, lbm_ba
         descs.push_back(c->d_desc);
         const int pr = is_fp32(c) ? 1 : 0, bi = c->bx == 128 ? 1 : 0;
         const int par = (int)(c->steps & 1);
-        auto w = make_work(c->cfg, i, c->bx, c->by, par);
+        auto w = make_work(c->cfg, i, c->bx, c->by, par, c->steps);
         groups[pr][bi].insert(groups[pr][bi].end(), w.begin(), w.end());
         auto bw = make_bwork(c->cfg, i, par);
         bgroups[pr].insert(bgroups[pr].end(), bw.begin(), bw.end());
@@ -1269,6 +1532,7 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, int graph_steps, lbm_ba
             b->w_cnt[pr][bi] = (int)groups[pr][bi].size();
             all.insert(all.end(), groups[pr][bi].begin(), groups[pr][bi].end());
         }
+    if (bgroups[0].empty() && bgroups[1].empty()) ensure_tick(bgroups[is_fp32(ctxs[0]) ? 1 : 0], 0, (int)(ctxs[0]->steps & 1));
     std::vector<BWork> ball;
     for (int pr = 0; pr < 2; ++pr) {
         b->b_off[pr] = (int)ball.size();
@@ -1280,6 +1544,8 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, int graph_steps, lbm_ba
         return fail(LBM_ECUDA, m);
     };
     if (cudaMalloc(&b->d_descs, descs.size() * sizeof(InstDesc*)) != cudaSuccess) return bad("cudaMalloc descs");
+    if (cudaMalloc(&b->d_counter, sizeof(long long)) != cudaSuccess) return bad("cudaMalloc counter");
+    if (cudaMemsetAsync(b->d_counter, 0, sizeof(long long), b->stream) != cudaSuccess) return bad("memset counter");
     if (!all.empty() && cudaMalloc(&b->d_work, all.size() * sizeof(Work)) != cudaSuccess) return bad("cudaMalloc work");
     if (!ball.empty() && cudaMalloc(&b->d_bwork, ball.size() * sizeof(BWork)) != cudaSuccess) return bad("cudaMalloc bwork");
     if (cudaMemcpyAsync(b->d_descs, descs.data(), descs.size() * sizeof(InstDesc*), cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
@@ -1311,6 +1577,9 @@ lbm_status lbm_batch_step(lbm_batch* b, long nsteps) {
     if (!b || nsteps < 0) return fail(LBM_EINVAL, "bad batch step");
     for (lbm_ctx* c : b->ctxs)
         if (c->sticky != LBM_OK) return fail(c->sticky, "a batch member is unstable");
+    if (nsteps == 0) return LBM_OK;
+    lbm_status cs = batch_set_counter(b);
+    if (cs != LBM_OK) return cs;
     if (b->graph) {
         if (nsteps % b->graph_steps) return fail(LBM_EINVAL, "nsteps must be a multiple of graph_steps");
         for (long s = 0; s < nsteps; s += b->graph_steps) CUDA_TRY(cudaGraphLaunch(b->graph, b->stream));
@@ -1335,22 +1604,14 @@ lbm_status lbm_batch_step_profiled(lbm_batch* b, long nsteps, double* ms_collide
     };
     for (auto& e : ev)
         if (cudaEventCreate(&e) != cudaSuccess) { cleanup(); return fail(LBM_ECUDA, "cudaEventCreate"); }
+    lbm_status cs = batch_set_counter(b);
+    if (cs != LBM_OK) { cleanup(); return cs; }
     for (long s = 0; s < nsteps; ++s) {
         const int par = (int)((b->steps + s) & 1);
         cudaEventRecord(ev[3 * s], b->stream);
-        for (int pr = 0; pr < 2; ++pr)
-            for (int bi = 0; bi < 2; ++bi) {
-                if (!b->w_cnt[pr][bi]) continue;
-                const int bx = bi ? 128 : 64;
-                if (pr) launch_collide<float>(b->d_work + b->w_off[pr][bi], b->w_cnt[pr][bi], bx, b->d_descs, par, b->stream);
-                else launch_collide<double>(b->d_work + b->w_off[pr][bi], b->w_cnt[pr][bi], bx, b->d_descs, par, b->stream);
-            }
+        batch_launch_collide(b, par);
         cudaEventRecord(ev[3 * s + 1], b->stream);
-        for (int pr = 0; pr < 2; ++pr) {
-            if (!b->b_cnt[pr]) continue;
-            if (pr) launch_boundary<float>(b->d_bwork + b->b_off[pr], b->b_cnt[pr], b->d_descs, par, b->stream);
-            else launch_boundary<double>(b->d_bwork + b->b_off[pr], b->b_cnt[pr], b->d_descs, par, b->stream);
-        }
+        batch_launch_boundary(b, par);
         cudaEventRecord(ev[3 * s + 2], b->stream);
     }
     lbm_status st = check_launch();
@@ -1377,6 +1638,7 @@ lbm_status lbm_batch_destroy(lbm_batch* b) {
     if (b->stream) cudaStreamSynchronize(b->stream);
     else cudaDeviceSynchronize();
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->d_counter) cudaFree(b->d_counter);
     if (b->d_descs) cudaFree(b->d_descs);
     if (b->d_work) cudaFree(b->d_work);
     if (b->d_bwork) cudaFree(b->d_bwork);

@@ -27,6 +27,17 @@
 
 namespace lbm {
 
+// Division and reciprocal: exact in FP64; in FP32 the fast hardware
+// division (a few ulp), which the FP32 path's 1e-4 tolerance absorbs.
+LBM_HD double fdiv(double a, double b) { return a / b; }
+LBM_HD float fdiv(float a, float b) {
+#if defined(__CUDA_ARCH__)
+    return __fdividef(a, b);
+#else
+    return a / b;
+#endif
+}
+
 // Constants of one lattice, in the arithmetic type R.
 template <typename R>
 struct Params {
@@ -71,7 +82,7 @@ LBM_HD R eos_dev(const Params<R>& P, R rho_d, R rho, R T_d, R T) {
         // [rho T (1 - b rho0) - rho0 T0 (1 - b rho)] = rho_d T + rho0 T_d - b rho rho0 T_d
         R om = R(1) - P.eos_b * rho;
         R num = rho_d * T + P.rho0 * T_d - P.eos_b * rho * P.rho0 * T_d;
-        return P.Rg * num / (om * P.cs_b0) - P.eos_a * rho_d * (rho + P.rho0);
+        return fdiv(P.Rg * num, om * P.cs_b0) - P.eos_a * rho_d * (rho + P.rho0);
     }
     }
 }
@@ -81,7 +92,7 @@ template <typename R>
 LBM_HD void macros(const Params<R>& P, R rho_d, R jx, R jy, R sg, Mac<R>& m) {
     m.rho_d = rho_d;
     m.rho = P.rho0 + rho_d;
-    m.ir = R(1) / m.rho;
+    m.ir = fdiv(R(1), m.rho);
     if (P.force_mode) { m.Fx = m.rho * P.Fx; m.Fy = m.rho * P.Fy; }
     else { m.Fx = P.Fx; m.Fy = P.Fy; }
     m.ux = (jx + R(0.5) * m.Fx) * m.ir;
@@ -92,7 +103,7 @@ LBM_HD void macros(const Params<R>& P, R rho_d, R jx, R jy, R sg, Mac<R>& m) {
     m.T_d = (E_d - R(0.5) * (m.ux * m.ux + m.uy * m.uy)) * P.inv_Cv;
     m.T = P.T0 + m.T_d;
     m.p_d = eos_dev(P, rho_d, m.rho, m.T_d, m.T);
-    m.eta_d = (R(3) * m.p_d - (R(2) + P.alpha1) * rho_d) / P.beta1;
+    m.eta_d = fdiv(R(3) * m.p_d - (R(2) + P.alpha1) * rho_d, P.beta1);
     m.rhoH = P.rho0E0_p0 + m.rhoE_d + m.p_d;
 }
 
@@ -131,7 +142,7 @@ LBM_HD R viscosity(const Params<R>& P, R T) {
     if (P.visc == 1) return P.mu0 * T * P.inv_T0;
     if (P.visc == 2) {
         R th = T * P.inv_T0;
-        return P.mu0 * th * sqrt(th) * (R(1) + P.visc_S) / (th + P.visc_S);
+        return fdiv(P.mu0 * th * sqrt(th) * (R(1) + P.visc_S), th + P.visc_S);
     }
     return P.mu0;
 }
@@ -140,12 +151,12 @@ template <typename R>
 LBM_HD void rates(const Params<R>& P, R rho_ir, R T, Rates<R>& r) {
     R mu = viscosity(P, T);
     R nu = mu * rho_ir;
-    r.sp = R(1) / (R(0.5) + R(3) * nu);
-    r.sq = R(36) * nu / (R(18) * nu + R(1));
-    r.se = R(1) / (R(0.5) + P.e_fac * nu);
+    r.sp = fdiv(R(1), R(0.5) + R(3) * nu);
+    r.sq = fdiv(R(36) * nu, R(18) * nu + R(1));
+    r.se = fdiv(R(1), R(0.5) + P.e_fac * nu);
     R a = P.lam_fac * mu * P.tj_fac;  // 1/sigma_j - 1/2
-    r.sj = R(1) / (R(0.5) + a);
-    r.sE = R(4) * a / (R(2) * a + R(1));
+    r.sj = fdiv(R(1), R(0.5) + a);
+    r.sE = fdiv(R(4) * a, R(2) * a + R(1));
 }
 
 // Rows 1, 2, 4, 6, 7, 8 of m - m^eq + F_m/2 (rows 0, 3, 5 vanish identically
@@ -263,10 +274,21 @@ LBM_HD void energy_eq(const Params<R>& P, const Mac<R>& m, EDev<R>& e) {
     e.Q5 = m.qe * m.uy;
 }
 
-// Full collision of one node: f, g hold deviations on entry and the
-// post-collision deviations f_bar', g_bar' on exit (Eqs. LBE.u.c, LBE.T.c).
-template <typename R>
-LBM_HD void collide(const Params<R>& P, const Mac<R>& mc, R* f, R* g, R grx, R gry, R gpx, R gpy) {
+// Plain update: new = old + delta, rounded to nearest.
+struct AddNearest {
+    template <typename R>
+    LBM_HD R operator()(R old, R delta) const { return old + delta; }
+};
+
+// Full collision of one node (Eqs. LBE.u.c, LBE.T.c) in increment form: the
+// moment changes m_bar - m and n_bar - n are formed from small quantities
+// only (force and source moments, non-equilibrium parts, corrections), then
+// mapped back with M^-1 and added to the stored deviations through `add`,
+// which may round stochastically.  f, g hold deviations on entry and the
+// post-collision deviations on exit.
+template <typename R, typename Add>
+LBM_HD void collide(const Params<R>& P, const Mac<R>& mc, R* f, R* g, R grx, R gry, R gpx, R gpy,
+                    const Add& add) {
     Rates<R> r;
     rates(P, mc.ir, mc.T, r);
     R m[9];
@@ -282,7 +304,7 @@ LBM_HD void collide(const Params<R>& P, const Mac<R>& mc, R* f, R* g, R grx, R g
     if (P.corrections) {
         R ux2 = ux * ux, uy2 = uy * uy, sum2 = ux2 + uy2, dif2 = ux2 - uy2, xy = ux * uy;
         R tse = R(2) - r.se, tsp = R(2) - r.sp;
-        R q1 = r.sp * tse / tsp, q7 = r.se * tsp / tse;
+        R q1 = fdiv(r.sp * tse, tsp), q7 = fdiv(r.se * tsp, tse);
         R R11 = P.cR11 * r.se * sum2;
         R R17 = P.cR17 * q1 * dif2;
         R R18 = P.cR18 * q1 * xy;
@@ -307,22 +329,22 @@ LBM_HD void collide(const Params<R>& P, const Mac<R>& mc, R* f, R* g, R grx, R g
         C8 = R81 * G.G1 + R88 * G.G8 + b8 * (v8x * (R(3) * gpx - grx) + v8y * (R(3) * gpy - gry));
     }
 
-    // m_bar = m + F_m - S d - C with S d = 2 (d - G)
-    R mb[9];
-    mb[0] = m[0];
-    mb[3] = m[3] + mc.Fx;
-    mb[5] = m[5] + mc.Fy;
-    mb[1] = m[1] + d.F1 - R(2) * d.d1 + R(2) * G.G1 - C1;
-    mb[2] = m[2] + d.F2 - R(2) * d.d2 + R(2) * G.G2;
-    mb[4] = m[4] + d.F4 - R(2) * d.d4 + R(2) * G.G4;
-    mb[6] = m[6] + d.F6 - R(2) * d.d6 + R(2) * G.G6;
-    mb[7] = m[7] + d.F7 - R(2) * d.d7 + R(2) * G.G7 - C7;
-    mb[8] = m[8] + d.F8 - R(2) * d.d8 + R(2) * G.G8 - C8;
+    // m_bar - m = F_m - S d - C with S d = 2 (d - G); rows 0, 3, 5: 0, Fx, Fy
+    R dm[9];
+    dm[0] = R(0);
+    dm[3] = mc.Fx;
+    dm[5] = mc.Fy;
+    dm[1] = d.F1 - R(2) * d.d1 + R(2) * G.G1 - C1;
+    dm[2] = d.F2 - R(2) * d.d2 + R(2) * G.G2;
+    dm[4] = d.F4 - R(2) * d.d4 + R(2) * G.G4;
+    dm[6] = d.F6 - R(2) * d.d6 + R(2) * G.G6;
+    dm[7] = d.F7 - R(2) * d.d7 + R(2) * G.G7 - C7;
+    dm[8] = d.F8 - R(2) * d.d8 + R(2) * G.G8 - C8;
 
     // (m + m_bar)/2 - m^eq on rows 1, 7, 8
     R Gt1 = G.G1 - R(0.5) * C1, Gt7 = G.G7 - R(0.5) * C7, Gt8 = G.G8 - R(0.5) * C8;
 
-    // total-energy DF: n_bar = n + Q - L (n - n^eq + Q/2) + Y ((m + m_bar)/2 - m^eq)
+    // total-energy DF: n_bar - n = Q - L (n - n^eq + Q/2) + Y ((m + m_bar)/2 - m^eq)
     R n[9];
     moments(g, n);
     EDev<R> e;
@@ -333,23 +355,33 @@ LBM_HD void collide(const Params<R>& P, const Mac<R>& mc, R* f, R* g, R grx, R g
     R dn4 = n[4] + e.ne3 - R(0.5) * e.Q3;
     R dn5 = n[5] - e.ne5 + R(0.5) * e.Q5;
     R dn6 = n[6] + e.ne5 - R(0.5) * e.Q5;
-    R dn7 = n[7], dn8 = n[8];
     R wj = R(0.5) * r.sj - R(1);
     R Y3 = ux * (Gt1 * R(1.0 / 3.0) + Gt7) + R(2) * uy * Gt8;
     R Y5 = uy * (Gt1 * R(1.0 / 3.0) - Gt7) + R(2) * ux * Gt8;
     R nb[9];
-    nb[0] = n[0] + e.Q0;
-    nb[1] = n[1] + e.Q1 - r.sE * dn1;
-    nb[2] = n[2] + e.Q2 - r.sE * dn2;
-    nb[3] = n[3] + e.Q3 - (r.sj * dn3 + r.sj * wj * dn4) + Y3;
-    nb[4] = n[4] - e.Q3 - r.sj * dn4 - Y3;
-    nb[5] = n[5] + e.Q5 - (r.sj * dn5 + r.sj * wj * dn6) + Y5;
-    nb[6] = n[6] - e.Q5 - r.sj * dn6 - Y5;
-    nb[7] = n[7] - r.sE * dn7;
-    nb[8] = n[8] - r.sE * dn8;
+    nb[0] = e.Q0;
+    nb[1] = e.Q1 - r.sE * dn1;
+    nb[2] = e.Q2 - r.sE * dn2;
+    nb[3] = e.Q3 - (r.sj * dn3 + r.sj * wj * dn4) + Y3;
+    nb[4] = -e.Q3 - r.sj * dn4 - Y3;
+    nb[5] = e.Q5 - (r.sj * dn5 + r.sj * wj * dn6) + Y5;
+    nb[6] = -e.Q5 - r.sj * dn6 - Y5;
+    nb[7] = -r.sE * n[7];
+    nb[8] = -r.sE * n[8];
 
-    inverse_moments(mb, f);
-    inverse_moments(nb, g);
+    R df[9], dg[9];
+    inverse_moments(dm, df);
+    inverse_moments(nb, dg);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        f[i] = add(f[i], df[i]);
+        g[i] = add(g[i], dg[i]);
+    }
+}
+
+template <typename R>
+LBM_HD void collide(const Params<R>& P, const Mac<R>& mc, R* f, R* g, R grx, R gry, R gpx, R gpy) {
+    collide(P, mc, f, g, grx, gry, gpx, gpy, AddNearest());
 }
 
 // Redefined non-equilibrium moments of Eq. (neq.redefinition) at a fluid

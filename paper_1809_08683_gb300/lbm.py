@@ -82,7 +82,7 @@ def load(path: str | None = None):
         if _lib is not None:
             return _lib
         if path is None:
-            path = LIB_PATH if os.path.exists(LIB_PATH) else build()
+            path = os.environ.get("LBM_LIBRARY") or (LIB_PATH if os.path.exists(LIB_PATH) else build())
         L = C.CDLL(path)
         P = C.POINTER
         vp, dp, i, cfgp = C.c_void_p, P(C.c_double), C.c_int, P(Config)

@@ -91,18 +91,50 @@ def cavity_gravity(N, Ra, eps, Pr=0.71, tau0=0.6):
     return Ra * mu0 * mu0 / (Pr * 2.0 * eps * L ** 3)
 
 
-def cavity(N=512, Ra=1e6, eps=0.6, Pr=0.71, gamma=1.4, tau0=0.6,
+def sutherland_ratio(theta, S=SUTHERLAND_S_OVER_T0):
+    """mu / mu0 at T / T0 = theta (Sec. 4.3, ratio form)."""
+    return theta * math.sqrt(theta) * (1.0 + S) / (theta + S)
+
+
+def tau_for(N, Ra, eps, tau_pref=0.6, dtau_cold=0.06, u_peak=0.065, u_peak_over_uref=0.32,
+            strat=0.15, Pr=0.71):
+    """Relaxation time at (rho0, T0) for a heated cavity of side N, and the
+    Rayleigh number actually run.
+
+    Lower bound: at the cold wall (T = 1 - eps, rho ~ 1/T, Sutherland mu) the
+    local 1/s_p - 1/2 stays >= dtau_cold.  Upper bound: the peak velocity,
+    about 0.32 U_ref with U_ref = sqrt(Ra) nu0 / L (Table 2), stays below
+    u_peak and the hydrostatic stratification 3 g L = 3 U_ref^2 / (Pr 2 eps)
+    below strat.  tau_pref is used when it satisfies both; when the bounds
+    conflict (Ra too high for the lattice), tau is the lower bound and Ra is
+    lowered to the largest value that meets the upper bound."""
+    L = N - 1
+    Tc = 1.0 - eps
+    lo = 0.5 + dtau_cold / (sutherland_ratio(Tc) * Tc)
+    uref_max = min(u_peak / u_peak_over_uref, math.sqrt(strat * Pr * 2.0 * eps / 3.0))
+    hi = 0.5 + 3.0 * L * uref_max / math.sqrt(Ra)
+    if lo <= hi:
+        return max(lo, min(tau_pref, hi)), Ra
+    return lo, (3.0 * L * uref_max / (lo - 0.5)) ** 2
+
+
+def cavity(N=512, Ra=1e6, eps=0.6, Pr=0.71, gamma=1.4, tau0=None,
            eos=(EOS_IDEAL, ()), precision=0, order=1):
     """Heated square cavity (Sec. 4.3): west wall hot T0(1+eps), east wall
     cold T0(1-eps), adiabatic south/north walls, all at rest; F = rho g with
-    g = (0, -g); Sutherland viscosity; first-order extrapolation."""
+    g = (0, -g); Sutherland viscosity; first-order extrapolation.  tau0=None
+    picks tau0 (and, if the lattice is too coarse, a lower Ra) by tau_for."""
+    Ra_req = Ra
+    if tau0 is None:
+        tau0, Ra = tau_for(N, Ra, eps, Pr=Pr)
     g = cavity_gravity(N, Ra, eps, Pr, tau0)
     return base(N, N, tau0=tau0, Pr=Pr, gamma=gamma, precision=precision,
                 visc_law=VISC_SUTHERLAND, visc_p=(SUTHERLAND_S_OVER_T0, 0.0),
                 bulk_ratio=bulk_ratio_for(Ra), force_mode=1, force=(0.0, -g),
                 walls=[wall((0, 0), 1.0, 1, order), wall((0, 0), 1.0, 1, order),
                        wall((0, 0), 1.0 + eps, 0, order), wall((0, 0), 1.0 - eps, 0, order)],
-                eos={"kind": int(eos[0]), "params": list(eos[1])}, Ra=float(Ra), eps=float(eps))
+                eos={"kind": int(eos[0]), "params": list(eos[1])}, Ra=float(Ra), Ra_requested=float(Ra_req),
+                eps=float(eps))
 
 
 def periodic_box(nx, ny, tau0=0.8, Pr=0.71, gamma=1.4, eos=(EOS_IDEAL, ()), precision=0,
@@ -176,4 +208,34 @@ def batched_sweep(n=96, seed=1809, precision=1, cap=1024):
         N = grid_for_Ra(Ra, cap)
         eos = (EOS_CUBIC, (0.05, 0.2)) if cubic else (EOS_IDEAL, ())
         out.append(cavity(N=N, Ra=Ra, eps=eps, eos=eos, precision=precision))
+    return out
+
+
+def serving_mix(n=2000, seed=1810, min_side=64, max_side=2048, mean_interarrival=0.05,
+                tol=1e-7, max_steps=2_000_000, precision=1):
+    """Poisson stream of cavity and channel solves: sides log-uniform in
+    [min_side, max_side], Ra log-linear in the side from 1e3 (64) to 1e8
+    (2048) for cavities, eps and EOS as in the batched sweep, channels of
+    4..64 periodic columns (Poiseuille with the same EOS mix).  Returns a list
+    of dicts {rid, cfg, arrival, tol, max_steps, kind}."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for rid in range(n):
+        t += rng.exponential(mean_interarrival)
+        side = int(round(math.exp(rng.uniform(math.log(min_side), math.log(max_side)))))
+        side = max(8, side)
+        eps = rng.uniform(0.1, 0.6)
+        cubic = rng.uniform() < 0.5
+        eos = (EOS_CUBIC, (0.05, 0.2)) if cubic else (EOS_IDEAL, ())
+        if rng.uniform() < 0.5:
+            Ra = 10 ** (3 + 5 * math.log(side / 64.0) / math.log(2048 / 64.0))
+            Ra = max(Ra, 1e3)
+            cfg = cavity(N=side, Ra=Ra, eps=eps, eos=eos, precision=precision)
+            kind = "cavity"
+        else:
+            nx = int(rng.integers(4, 65))
+            cfg = poiseuille(nx=nx, ny=side, eos=eos, gamma=1.3 if cubic else 1.4, precision=precision)
+            kind = "channel"
+        out.append({"rid": rid, "cfg": cfg, "arrival": t, "tol": tol, "max_steps": max_steps, "kind": kind})
     return out

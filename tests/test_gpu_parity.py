@@ -29,8 +29,10 @@ def rel(a, b, floor=1e-12):
 
 
 def field_errors(mg, mo):
-    return {"rho": rel(mg["rho"], mo["rho"]), "ux": rel(mg["ux"], mo["ux"]),
-            "uy": rel(mg["uy"], mo["uy"]), "T": rel(mg["T"], mo["T"])}
+    # velocity errors relative to the max norm of the velocity vector field
+    umax = max(np.hypot(mo["ux"], mo["uy"]).max(), 1e-12)
+    return {"rho": rel(mg["rho"], mo["rho"]), "ux": np.abs(mg["ux"] - mo["ux"]).max() / umax,
+            "uy": np.abs(mg["uy"] - mo["uy"]).max() / umax, "T": rel(mg["T"], mo["T"])}
 
 
 def pair(orc, lbm, cfg, steps, seed=None, df=0.0, tile=None):
@@ -101,7 +103,7 @@ def test_poiseuille_config2_fp64(orc, lbm):
 
 @pytest.mark.parametrize("tile", [None, (64, 3), (128, 64)])
 def test_cavity_fp64(orc, lbm, tile):
-    cfg = W.cavity(N=64, Ra=1e3, eps=0.6, tau0=0.6)
+    cfg = W.cavity(N=64, Ra=1e3, eps=0.6)
     _, _, err = pair(orc, lbm, cfg, 1000, tile=tile)
     assert_close(err, TOL64)
 
@@ -131,7 +133,7 @@ def test_minimal_walled_lattice_fp64(orc, lbm):
 
 def test_cavity_512_bench_shape_fp64(orc, lbm):
     # full-size configuration (512^2, Ra 1e6) in the default launch shape
-    cfg = W.cavity(N=512, Ra=1e6, eps=0.6, tau0=0.6)
+    cfg = W.cavity(N=512, Ra=1e6, eps=0.6)
     _, _, err = pair(orc, lbm, cfg, 20)
     assert_close(err, TOL64)
 
@@ -152,7 +154,7 @@ def test_couette_config1_fp32(orc, lbm):
 
 
 def test_cavity_fp32(orc, lbm):
-    cfg = W.cavity(N=64, Ra=1e3, eps=0.6, tau0=0.6, precision=1)
+    cfg = W.cavity(N=64, Ra=1e3, eps=0.6, precision=1)
     o, g, err = pair(orc, lbm, cfg, 2000)
     assert_close(err, TOL32)
     assert abs(g.nusselt(W.WALL_W) / o.nusselt(W.WALL_W) - 1) < 5e-3
@@ -204,7 +206,7 @@ def test_nan_injection_reports_unstable(lbm):
 
 def _mixed_lattices(lbm):
     cfgs = [W.cavity(N=40, Ra=1e3, eps=0.6, tau0=0.7),
-            W.cavity(N=70, Ra=2e3, eps=0.3, tau0=0.6, eos=(W.EOS_CUBIC, (0.05, 0.2)), precision=1),
+            W.cavity(N=70, Ra=2e3, eps=0.3, eos=(W.EOS_CUBIC, (0.05, 0.2)), precision=1),
             W.poiseuille(nx=5, ny=33),
             W.couette(nx=130, ny=12, precision=1)]
     return cfgs
@@ -219,7 +221,7 @@ def test_batch_equals_alone(lbm, graph_steps):
     mixed = [lbm.Lattice(c, stream=stream) for c in cfgs]
     alone[1].set_tile(64, 9)
     mixed[1].set_tile(64, 9)
-    for a in alone:
+    for a in alone[:2]:
         a.step(7)        # odd step count: the batch must respect each lattice's parity
     for m in mixed[:2]:
         m.step(7)
