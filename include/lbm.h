@@ -140,8 +140,8 @@ lbm_status lbm_init_macros(lbm_ctx* ctx, const double* rho, const double* ux,
 /* Derived constants: R, Cv, Cp, mu0, p0, eta0, lambda0, c_s^2. */
 lbm_status lbm_derived(const lbm_ctx* ctx, double* out8);
 
-/* Launch shape of the fused kernel: strip width bx (64 or 128 threads) and
- * rows per CTA by (>= 1).  Used by the autotuner. */
+/* Launch shape of the fused kernel: strip width bx (32, 64 or 128 threads,
+ * one CTA per strip) and rows per CTA by (>= 1).  Used by the autotuner. */
 lbm_status lbm_set_tile(lbm_ctx* ctx, int bx, int by);
 
 /* Steps taken since the last (re)initialisation. */

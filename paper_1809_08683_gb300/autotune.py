@@ -1,6 +1,6 @@
 """Launch-shape autotuner for the fused collide-stream kernel.
 
-The fused kernel gives each CTA a strip of ``bx`` columns (64 or 128
+The fused kernel gives each CTA a strip of ``bx`` columns (32, 64 or 128
 threads) and a run of ``by`` rows that it sweeps with a three-row ring of
 rho' and p' in shared memory.  Short runs give more CTAs (better SM fill on
 small lattices) but re-read two halo rows per run; long runs amortise the
@@ -20,7 +20,7 @@ from . import lbm
 _CACHE_PATH = os.environ.get(
     "LBM_TUNE_CACHE", os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tile_cache.json"))
 _lock = threading.Lock()
-BX_CANDIDATES = (64, 128)
+BX_CANDIDATES = (32, 64, 128)
 BY_CANDIDATES = (4, 8, 16, 32, 64, 128)
 
 
@@ -55,7 +55,7 @@ def _store(d):
 def candidates(cfg: dict):
     out = []
     for bx in BX_CANDIDATES:
-        if bx == 128 and cfg["nx"] <= 64:
+        if bx > 32 and cfg["nx"] <= bx // 2:
             continue
         for by in BY_CANDIDATES:
             if by > cfg["ny"] and by != BY_CANDIDATES[0]:

@@ -217,8 +217,17 @@ struct FusedSmem {
     static constexpr size_t bytes = off_ring + (size_t)2 * 4 * (BX + 2) * sizeof(R);
 };
 
+// Launch traits of the fused kernel: stage count (rows in flight = S - 2
+// beyond the two being used) and the minimum resident CTAs per SM, which caps
+// registers at 128 (FP32) or 255 (FP64) per thread.
+template <typename R, int BX>
+struct FusedTraits {
+    static constexpr int S = BX == 32 ? 3 : 4;
+    static constexpr int MINB = (sizeof(R) == 4 ? 512 : 256) / BX;
+};
+
 template <typename R, int BX, int S>
-__global__ void __launch_bounds__(BX) k_collide_stream(const Work* __restrict__ work,
+__global__ void __launch_bounds__(BX, FusedTraits<R, BX>::MINB) k_collide_stream(const Work* __restrict__ work,
                                                        InstDesc* const* __restrict__ descs, int step_par,
                                                        const long long* __restrict__ counter) {
     using L = FusedSmem<R, BX, S>;
@@ -315,23 +324,28 @@ __global__ void __launch_bounds__(BX) k_collide_stream(const Work* __restrict__ 
             s_rho[slot][c] = m.rho_d;
             s_p[slot][c] = m.p_d;
         }
-        if (tid == 0 && has_l) {
+        // the two halo columns: lane 0 of warp 0 and the strip's last thread
+        // run the same instruction stream on their own chunk
+        const bool hl = (tid == 0 && has_l), hr = (tid == tlast && has_r);
+        if (hl || hr) {
+            const int off = hl ? (xhl - xcl) : (E + BX + (xhr - xcr));
+            const int col = hl ? 0 : tlast + 2;
             R v[18];
 #pragma unroll
-            for (int q = 0; q < 18; ++q) v[q] = st[q * W + (xhl - xcl)];
+            for (int q = 0; q < 18; ++q) v[q] = st[q * W + off];
             Mac<R> h;
             node_macros(P, v, h);
-            s_rho[slot][0] = h.rho_d;
-            s_p[slot][0] = h.p_d;
-        }
-        if (tid == tlast && has_r) {
-            R v[18];
+            s_rho[slot][col] = h.rho_d;
+            s_p[slot][col] = h.p_d;
+            if (hl && hr && tlast == 0) {
+                // a one-column strip owns both halos in the same thread
+                const int off2 = E + BX + (xhr - xcr);
 #pragma unroll
-            for (int q = 0; q < 18; ++q) v[q] = st[q * W + E + BX + (xhr - xcr)];
-            Mac<R> h;
-            node_macros(P, v, h);
-            s_rho[slot][tlast + 2] = h.rho_d;
-            s_p[slot][tlast + 2] = h.p_d;
+                for (int q = 0; q < 18; ++q) v[q] = st[q * W + off2];
+                node_macros(P, v, h);
+                s_rho[slot][2] = h.rho_d;
+                s_p[slot][2] = h.p_d;
+            }
         }
         return true;
     };
@@ -403,14 +417,16 @@ __global__ void __launch_bounds__(BX) k_collide_stream(const Work* __restrict__ 
 
             R* o = dst + ((long long)j * pitch + x);
             if (x >= 1 && x <= nx - 2 && j >= 1 && j <= ny - 2) {
-                // interior: every population lands in the domain, no wrap
+                // interior: every population lands in the domain, no wrap;
+                // 18 planes fit 32-bit offsets (checked at creation)
+                const int pl = (int)plane;
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
                     const int ex = (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
                     const int ey = (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
                     const int off = ey * pitch + ex;
-                    o[i * plane + off] = v[i];
-                    o[(9 + i) * plane + off] = v[9 + i];
+                    o[i * pl + off] = v[i];
+                    o[(9 + i) * pl + off] = v[9 + i];
                 }
             } else {
                 // edge node: periodic wrap, or bounce-back into its own slot
@@ -836,7 +852,8 @@ lbm_status validate(const lbm_config* c) {
     if (px != pxe || py != pyn) return fail(LBM_EINVAL, "a periodic side must face a periodic side");
     if (c->nx < 1 || c->ny < 1) return fail(LBM_EINVAL, "nx, ny must be >= 1");
     if ((!px && c->nx < 4) || (!py && c->ny < 4)) return fail(LBM_EINVAL, "walled extents need >= 4 nodes");
-    if ((long long)c->nx * c->ny > (1LL << 31)) return fail(LBM_EINVAL, "lattice too large");
+    if (18LL * (long long)(((c->nx + 31) / 32) * 32) * c->ny >= (1LL << 31))
+        return fail(LBM_EINVAL, "lattice too large: 18 planes must fit 32-bit offsets");
     if (c->precision != LBM_FP64 && c->precision != LBM_FP32_DEV) return fail(LBM_EINVAL, "bad precision");
     for (int s = 0; s < 4; ++s) {
         if (c->wall[s].periodic) continue;
@@ -907,7 +924,7 @@ struct lbm_batch {
     Work* d_work = nullptr;
     BWork* d_bwork = nullptr;
     // launch groups: [precision][bx index] ranges of d_work; [precision] ranges of d_bwork
-    int w_off[2][2] = {{0, 0}, {0, 0}}, w_cnt[2][2] = {{0, 0}, {0, 0}};
+    int w_off[2][3] = {{0, 0, 0}, {0, 0, 0}}, w_cnt[2][3] = {{0, 0, 0}, {0, 0, 0}};
     int b_off[2] = {0, 0}, b_cnt[2] = {0, 0};
     long steps = 0;
     int graph_steps = 0;
@@ -977,15 +994,14 @@ lbm_status upload_work(lbm_ctx* c) {
     return LBM_OK;
 }
 
-constexpr int kStages = 4;
-
 template <typename R, int BX>
 cudaError_t configure_collide() {
-    cudaError_t e = cudaFuncSetAttribute(k_collide_stream<R, BX, kStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)FusedSmem<R, BX, kStages>::bytes);
+    constexpr int S = FusedTraits<R, BX>::S;
+    cudaError_t e = cudaFuncSetAttribute(k_collide_stream<R, BX, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)FusedSmem<R, BX, S>::bytes);
     if (e != cudaSuccess) return e;
     // prefer shared memory over L1: the row stages, not L1, feed the kernel
-    return cudaFuncSetAttribute(k_collide_stream<R, BX, kStages>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    return cudaFuncSetAttribute(k_collide_stream<R, BX, S>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                 (int)cudaSharedmemCarveoutMaxShared);
 }
 
@@ -994,8 +1010,10 @@ cudaError_t configure_collide() {
 lbm_status configure_kernels() {
     static int done = 0;
     if (done) return LBM_OK;
-    cudaError_t e = configure_collide<float, 64>();
+    cudaError_t e = configure_collide<float, 32>();
+    if (e == cudaSuccess) e = configure_collide<float, 64>();
     if (e == cudaSuccess) e = configure_collide<float, 128>();
+    if (e == cudaSuccess) e = configure_collide<double, 32>();
     if (e == cudaSuccess) e = configure_collide<double, 64>();
     if (e == cudaSuccess) e = configure_collide<double, 128>();
     if (e != cudaSuccess) return fail(LBM_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
@@ -1006,14 +1024,16 @@ lbm_status configure_kernels() {
 template <typename R, int BX>
 void launch_collide_bx(const Work* work, int n, InstDesc* const* descs, int par, const long long* counter,
                        cudaStream_t s) {
-    k_collide_stream<R, BX, kStages><<<n, BX, FusedSmem<R, BX, kStages>::bytes, s>>>(work, descs, par, counter);
+    constexpr int S = FusedTraits<R, BX>::S;
+    k_collide_stream<R, BX, S><<<n, BX, FusedSmem<R, BX, S>::bytes, s>>>(work, descs, par, counter);
 }
 
 template <typename R>
 void launch_collide(const Work* work, int n, int bx, InstDesc* const* descs, int par, const long long* counter,
                     cudaStream_t s) {
     if (n <= 0) return;
-    if (bx == 64) launch_collide_bx<R, 64>(work, n, descs, par, counter, s);
+    if (bx == 32) launch_collide_bx<R, 32>(work, n, descs, par, counter, s);
+    else if (bx == 64) launch_collide_bx<R, 64>(work, n, descs, par, counter, s);
     else launch_collide_bx<R, 128>(work, n, descs, par, counter, s);
 }
 
@@ -1285,7 +1305,7 @@ lbm_status lbm_derived(const lbm_ctx* c, double* out8) {
 
 lbm_status lbm_set_tile(lbm_ctx* c, int bx, int by) {
     if (!c) return fail(LBM_EINVAL, "null ctx");
-    if (bx != 64 && bx != 128) return fail(LBM_EINVAL, "bx must be 64 or 128");
+    if (bx != 32 && bx != 64 && bx != 128) return fail(LBM_EINVAL, "bx must be 32, 64 or 128");
     if (by < 1) return fail(LBM_EINVAL, "by must be >= 1");
     c->bx = bx;
     c->by = std::min(by, c->cfg.ny);
@@ -1468,10 +1488,14 @@ lbm_status lbm_diagnostics(lbm_ctx* c, int snapshot, double* out8) {
 // batched stepping
 // ------------------------------------------------------------------------
 
+static const int kWidths[3] = {32, 64, 128};
+
+static int width_index(int bx) { return bx == 32 ? 0 : (bx == 64 ? 1 : 2); }
+
 static void batch_launch_collide(lbm_batch* b, int par) {
     for (int pr = 0; pr < 2; ++pr)
-        for (int bi = 0; bi < 2; ++bi) {
-            const int bx = bi ? 128 : 64;
+        for (int bi = 0; bi < 3; ++bi) {
+            const int bx = kWidths[bi];
             if (!b->w_cnt[pr][bi]) continue;
             if (pr)
                 launch_collide<float>(b->d_work + b->w_off[pr][bi], b->w_cnt[pr][bi], bx, b->d_descs, par, b->d_counter, b->stream);
@@ -1508,7 +1532,7 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, int graph_steps, lbm_ba
     lbm_batch* b = new lbm_batch();
     b->stream = ctxs[0]->stream;
     std::vector<InstDesc*> descs;
-    std::vector<Work> groups[2][2];
+    std::vector<Work> groups[2][3];
     std::vector<BWork> bgroups[2];
     for (int i = 0; i < n; ++i) {
         lbm_ctx* c = ctxs[i];
@@ -1518,7 +1542,7 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, int graph_steps, lbm_ba
         }
         b->ctxs.push_back(c);
         descs.push_back(c->d_desc);
-        const int pr = is_fp32(c) ? 1 : 0, bi = c->bx == 128 ? 1 : 0;
+        const int pr = is_fp32(c) ? 1 : 0, bi = width_index(c->bx);
         const int par = (int)(c->steps & 1);
         auto w = make_work(c->cfg, i, c->bx, c->by, par, c->steps);
         groups[pr][bi].insert(groups[pr][bi].end(), w.begin(), w.end());
@@ -1527,7 +1551,7 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, int graph_steps, lbm_ba
     }
     std::vector<Work> all;
     for (int pr = 0; pr < 2; ++pr)
-        for (int bi = 0; bi < 2; ++bi) {
+        for (int bi = 0; bi < 3; ++bi) {
             b->w_off[pr][bi] = (int)all.size();
             b->w_cnt[pr][bi] = (int)groups[pr][bi].size();
             all.insert(all.end(), groups[pr][bi].begin(), groups[pr][bi].end());

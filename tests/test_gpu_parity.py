@@ -68,7 +68,7 @@ def test_periodic_small_fp64(orc, lbm, nx, ny):
     assert_close(err, TOL64)
 
 
-@pytest.mark.parametrize("bx,by", [(64, 1), (64, 5), (128, 37), (128, 4)])
+@pytest.mark.parametrize("bx,by", [(32, 1), (32, 37), (64, 1), (64, 5), (128, 37), (128, 4)])
 def test_periodic_multitile_ragged_fp64(orc, lbm, bx, by):
     cfg = W.periodic_box(200, 37, visc_law=1, eos=(W.EOS_IDEAL, ()), force=(2e-5, 0.0))
     _, _, err = pair(orc, lbm, cfg, 60, seed=17, df=1e-4, tile=(bx, by))
@@ -101,7 +101,7 @@ def test_poiseuille_config2_fp64(orc, lbm):
     assert_close(err, TOL64)
 
 
-@pytest.mark.parametrize("tile", [None, (64, 3), (128, 64)])
+@pytest.mark.parametrize("tile", [None, (32, 16), (64, 3), (128, 64)])
 def test_cavity_fp64(orc, lbm, tile):
     cfg = W.cavity(N=64, Ra=1e3, eps=0.6)
     _, _, err = pair(orc, lbm, cfg, 1000, tile=tile)
@@ -221,6 +221,8 @@ def test_batch_equals_alone(lbm, graph_steps):
     mixed = [lbm.Lattice(c, stream=stream) for c in cfgs]
     alone[1].set_tile(64, 9)
     mixed[1].set_tile(64, 9)
+    alone[3].set_tile(32, 5)
+    mixed[3].set_tile(32, 5)
     for a in alone[:2]:
         a.step(7)        # odd step count: the batch must respect each lattice's parity
     for m in mixed[:2]:
