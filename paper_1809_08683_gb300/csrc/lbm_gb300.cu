@@ -117,14 +117,21 @@ __device__ __forceinline__ uint32_t mix32(uint32_t h) {
 
 struct AddDither {
     mutable uint32_t h;
-    __device__ __forceinline__ float operator()(float old, float delta) const {
-        h = h * 1664525u + 1013904223u;                       // one LCG step per store
-        const float r = (float)(int)h * 2.3283064365386963e-10f;  // uniform in [-1/2, 1/2)
-        const int e = (__float_as_int(old) & 0x7f800000) - (23 << 23);
-        const float ulp = __int_as_float(e > 0 ? e : 0);
-        return old + fmaf(r, ulp, delta);
+    // f_i and g_i are independent variables, so one uniform draw serves both
+    __device__ __forceinline__ void operator()(float& f, float df, float& g, float dg) const {
+        h = h * 1664525u + 1013904223u;  // one LCG step per link
+        // 23 random mantissa bits: uniform in [1, 2), shifted to [-1/2, 1/2)
+        const float r = __int_as_float(0x3f800000u | (h >> 9)) - 1.5f;
+        // ulp of a normal float: 2^(exponent - 23); zero for zero
+        const float uf = __int_as_float(__float_as_int(f) & 0x7f800000) * 1.1920928955078125e-7f;
+        const float ug = __int_as_float(__float_as_int(g) & 0x7f800000) * 1.1920928955078125e-7f;
+        f = f + fmaf(r, uf, df);
+        g = g + fmaf(r, ug, dg);
     }
-    __device__ __forceinline__ double operator()(double old, double delta) const { return old + delta; }
+    __device__ __forceinline__ void operator()(double& f, double df, double& g, double dg) const {
+        f = f + df;
+        g = g + dg;
+    }
 };
 
 // rho' and p' of node (xx, yy) read straight from a buffer.

@@ -274,10 +274,14 @@ LBM_HD void energy_eq(const Params<R>& P, const Mac<R>& m, EDev<R>& e) {
     e.Q5 = m.qe * m.uy;
 }
 
-// Plain update: new = old + delta, rounded to nearest.
+// Plain update: new = old + delta, rounded to nearest, for the pair
+// (f_i, g_i) of one link.
 struct AddNearest {
     template <typename R>
-    LBM_HD R operator()(R old, R delta) const { return old + delta; }
+    LBM_HD void operator()(R& f, R df, R& g, R dg) const {
+        f = f + df;
+        g = g + dg;
+    }
 };
 
 // Full collision of one node (Eqs. LBE.u.c, LBE.T.c) in increment form: the
@@ -373,10 +377,7 @@ LBM_HD void collide(const Params<R>& P, const Mac<R>& mc, R* f, R* g, R grx, R g
     inverse_moments(dm, df);
     inverse_moments(nb, dg);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        f[i] = add(f[i], df[i]);
-        g[i] = add(g[i], dg[i]);
-    }
+    for (int i = 0; i < 9; ++i) add(f[i], df[i], g[i], dg[i]);
 }
 
 template <typename R>

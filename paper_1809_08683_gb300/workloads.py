@@ -101,25 +101,26 @@ def sutherland_ratio(theta, S=SUTHERLAND_S_OVER_T0):
     return theta * math.sqrt(theta) * (1.0 + S) / (theta + S)
 
 
-def tau_for(N, Ra, eps, tau_pref=0.6, dtau_cold=0.04, u_peak=0.065, u_peak_over_uref=0.32,
+def tau_for(N, Ra, eps, tau_min=0.65, dtau_cold=0.045, u_peak=0.065, u_peak_over_uref=0.32,
             strat=0.15, Pr=0.71):
     """Relaxation time at (rho0, T0) for a heated cavity of side N, and the
     Rayleigh number actually run.
 
-    Lower bound: at the cold wall (T = 1 - eps, rho ~ 1/T, Sutherland mu) the
-    local 1/s_p - 1/2 stays >= dtau_cold.  Upper bound: the peak velocity,
-    about 0.32 U_ref with U_ref = sqrt(Ra) nu0 / L (Table 2), stays below
-    u_peak and the hydrostatic stratification 3 g L = 3 U_ref^2 / (Pr 2 eps)
-    below strat.  tau_pref is used when it satisfies both; when the bounds
-    conflict (Ra too high for the lattice), tau is the lower bound and Ra is
-    lowered to the largest value that meets the upper bound."""
+    Lower bound: tau0 >= tau_min, and at the cold wall (T = 1 - eps,
+    rho ~ 1/T, Sutherland mu) the local 1/s_p - 1/2 stays >= dtau_cold.
+    Upper bound: the peak velocity, about 0.32 U_ref with
+    U_ref = sqrt(Ra) nu0 / L (Table 2), stays below u_peak and the hydrostatic
+    stratification 3 g L = 3 U_ref^2 / (Pr 2 eps) below strat.  tau0 is the
+    lower bound; when it exceeds the upper bound (Ra too high for the
+    lattice), Ra is lowered to the largest value that meets it.  The bounds
+    come from GPU stability scans of eps up to 0.6 with varsigma/nu = 4."""
     L = N - 1
     Tc = 1.0 - eps
-    lo = 0.5 + dtau_cold / (sutherland_ratio(Tc) * Tc)
+    lo = max(tau_min, 0.5 + dtau_cold / (sutherland_ratio(Tc) * Tc))
     uref_max = min(u_peak / u_peak_over_uref, math.sqrt(strat * Pr * 2.0 * eps / 3.0))
     hi = 0.5 + 3.0 * L * uref_max / math.sqrt(Ra)
     if lo <= hi:
-        return max(lo, min(tau_pref, hi)), Ra
+        return lo, Ra
     return lo, (3.0 * L * uref_max / (lo - 0.5)) ** 2
 
 
