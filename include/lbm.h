@@ -163,6 +163,29 @@ lbm_status lbm_batch_destroy(lbm_batch* b);     /* NULL-safe */
  * *ms_collide and *ms_wall receive their summed device times.  Synchronises. */
 lbm_status lbm_batch_step_profiled(lbm_batch* b, long nsteps, double* ms_collide, double* ms_wall);
 
+/* Conserved sums of a context's current state, computed without allocating
+ * anything.  The paper has no counterpart: this entry point is for callers
+ * that may not allocate device memory, for example a host program that
+ * only receives device buffers and a stream from another framework's
+ * allocator, or code that runs where cudaMalloc is not permitted.
+ *
+ * out4 is a caller-owned device array of 4 doubles receiving, in FP64:
+ *   out4[0] total mass sum(rho), out4[1] sum(j_x), out4[2] sum(j_y),
+ *   out4[3] sum over nodes of sum_i g_i (the total energy minus half the
+ *   source work, so equal to the total energy when F = 0).
+ * Asynchronous on the context's stream; the context's device must be current.
+ *
+ * Scratch: block partials go to a file-scope static device array of 2048 x 4
+ * doubles (64 KiB) that every GPU loading the library holds until exit.
+ * Lattices of more than 2048 x 32768 = 67,108,864 nodes are rejected with
+ * LBM_EINVAL.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  No cudaMalloc, cudaFree or allocating library routine is called.
+ * All calls share the one array and each call overwrites the slots it
+ * reads, so calls that overlap on the GPU (on different streams, or from
+ * several threads at once) race and must be serialised by the caller. */
+lbm_status lbm_conserved_sums_static(const lbm_ctx* ctx, double* out4);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,6 +23,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -768,6 +769,69 @@ __global__ void k_diag_final(const double* __restrict__ partials, int nblocks, d
     out[s] = v;
 }
 
+// ------------------------------------------------------------------------
+// conserved sums with statically allocated scratch (lbm_conserved_sums_static)
+// ------------------------------------------------------------------------
+
+// Block partials of lbm_conserved_sums_static live in this file-scope array
+// instead of caller- or library-allocated memory.  Every GPU that loads the
+// library holds it until the process exits.  Each block covers a fixed,
+// contiguous range of kStaticNodesPerBlock nodes, so the lattice size sets
+// how many slots are used.
+constexpr int kStaticBlocks = 2048;
+constexpr int kStaticThreads = 256;
+constexpr long long kStaticNodesPerBlock = 32768;
+static __device__ __align__(256) double g_static_partials[kStaticBlocks * 4];
+
+template <typename R>
+__global__ void __launch_bounds__(kStaticThreads) k_sums_static(const InstDesc* D, int b, double* __restrict__ partials) {
+    const long long nn = (long long)D->nx * D->ny;
+    const R* buf = reinterpret_cast<const R*>(D->buf[b]);
+    const long long lo = blockIdx.x * kStaticNodesPerBlock;
+    const long long hi = lo + kStaticNodesPerBlock < nn ? lo + kStaticNodesPerBlock : nn;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (long long t = lo + threadIdx.x; t < hi; t += kStaticThreads) {
+        const int y = (int)(t / D->nx), x = (int)(t % D->nx);
+        R v[18];
+        load18(buf, D->plane, (long long)y * D->pitch + x, v);
+        double w[18];
+#pragma unroll
+        for (int q = 0; q < 18; ++q) w[q] = (double)v[q];
+        double rd, jx, jy, sg;
+        lbm::node_sums(w, w + 9, rd, jx, jy, sg);
+        acc[0] += rd;
+        acc[1] += jx;
+        acc[2] += jy;
+        acc[3] += sg;
+    }
+    __shared__ double red[kStaticThreads / 32][4];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const double v = warp_sum(acc[s]);
+        if (lane == 0) red[wid][s] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double v = 0.0;
+        for (int k = 0; k < kStaticThreads / 32; ++k) v += red[k][threadIdx.x];
+        partials[blockIdx.x * 4 + threadIdx.x] = v;
+    }
+}
+
+__global__ void k_sums_static_final(const InstDesc* D, const double* __restrict__ partials, int nblocks,
+                                    double* __restrict__ out4) {
+    const int s = threadIdx.x;
+    if (s >= 4) return;
+    double v = 0.0;
+    for (int k = 0; k < nblocks; ++k) v += partials[k * 4 + s];
+    const double nn = (double)D->nx * D->ny;
+    // the rest equilibria carry rho0 and rho0 E0 per node and no momentum
+    if (s == 0) v += nn * D->pd.rho0;
+    if (s == 3) v += nn * D->pd.rho0 * D->pd.E0;
+    out4[s] = v;
+}
+
 // Mean Nusselt number through one wall: one block, fixed-order tree.
 template <typename R>
 __global__ void __launch_bounds__(1024) k_nusselt(const InstDesc* D, int b, int wall, double dT, double* out) {
@@ -1489,6 +1553,52 @@ lbm_status lbm_diagnostics(lbm_ctx* c, int snapshot, double* out8) {
         return fail(LBM_EUNSTABLE, "non-finite nodes in the state");
     }
     return read_status(c);
+}
+
+// ------------------------------------------------------------------------
+// conserved sums without allocation
+// ------------------------------------------------------------------------
+
+// Device address of g_static_partials, looked up once per device.  In host
+// code the array's name is only a host-side stand-in, so the kernels are
+// given the address that cudaGetSymbolAddress returns for the current device.
+static std::mutex g_static_mu;
+static double* g_static_addr[64] = {nullptr};
+
+static lbm_status static_scratch(double** out) {
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(LBM_EINVAL, "device index out of range");
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_partials);
+        if (e != cudaSuccess || !p)
+            return fail(LBM_ECUDA, std::string("cudaGetSymbolAddress(g_static_partials): ") + cudaGetErrorString(e));
+        g_static_addr[dev] = static_cast<double*>(p);
+    }
+    *out = g_static_addr[dev];
+    return LBM_OK;
+}
+
+lbm_status lbm_conserved_sums_static(const lbm_ctx* c, double* out4) {
+    if (!c || !c->eos_set || !out4) return fail(LBM_EINVAL, "context not initialised or null output");
+    const long long nn = (long long)c->cfg.nx * c->cfg.ny;
+    const long long nblocks = (nn + kStaticNodesPerBlock - 1) / kStaticNodesPerBlock;
+    if (nblocks > kStaticBlocks)
+        return fail(LBM_EINVAL, "lbm_conserved_sums_static handles at most " +
+                                    std::to_string((long long)kStaticBlocks * kStaticNodesPerBlock) +
+                                    " nodes; use lbm_diagnostics for larger lattices");
+    double* scratch = nullptr;
+    lbm_status st = static_scratch(&scratch);
+    if (st != LBM_OK) return st;
+    // every slot the final pass reads is written first, so nothing needs clearing
+    if (is_fp32(c))
+        k_sums_static<float><<<(int)nblocks, kStaticThreads, 0, c->stream>>>(c->d_desc, cur_buf(c), scratch);
+    else
+        k_sums_static<double><<<(int)nblocks, kStaticThreads, 0, c->stream>>>(c->d_desc, cur_buf(c), scratch);
+    k_sums_static_final<<<1, 32, 0, c->stream>>>(c->d_desc, scratch, (int)nblocks, out4);
+    return check_launch();
 }
 
 // ------------------------------------------------------------------------

@@ -72,7 +72,7 @@ EXPORTS = ("lbm_workspace_bytes", "lbm_create", "lbm_set_eos", "lbm_step", "lbm_
            "lbm_macros_device", "lbm_nusselt", "lbm_diagnostics", "lbm_get_state", "lbm_set_state",
            "lbm_init_macros", "lbm_derived", "lbm_set_tile", "lbm_step_count", "lbm_destroy",
            "lbm_last_error", "lbm_batch_create", "lbm_batch_step", "lbm_batch_step_profiled",
-           "lbm_batch_destroy")
+           "lbm_batch_destroy", "lbm_conserved_sums_static")
 
 
 def load(path: str | None = None):
@@ -109,6 +109,7 @@ def load(path: str | None = None):
         L.lbm_batch_step.argtypes = [vp, C.c_long]
         L.lbm_batch_step_profiled.argtypes = [vp, C.c_long, dp, dp]
         L.lbm_batch_destroy.argtypes = [vp]
+        L.lbm_conserved_sums_static.argtypes = [vp, vp]
         _lib = L
         return L
 
@@ -260,6 +261,11 @@ class Lattice:
 
     def set_tile(self, bx: int, by: int):
         _check(self.L, self.L.lbm_set_tile(self.h, int(bx), int(by)))
+
+    def conserved_sums_static(self, out):
+        """Total mass, x and y momentum and sum of g into the device tensor
+        ``out`` (4 doubles) without any allocation; asynchronous."""
+        _check(self.L, self.L.lbm_conserved_sums_static(self.h, C.c_void_p(out.data_ptr())))
 
 
 class Batch:
