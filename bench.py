@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--chunk", type=int, default=None, help="time steps per bench step")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--tile", default=None, help="bx,by[,pair] for every lattice (default: built-in)")
+    ap.add_argument("--serving", type=int, default=16,
+                    help="requests in the bounded serving run (0 to skip)")
     return ap.parse_args()
 
 
@@ -161,6 +164,44 @@ def cpu_baseline(cfgs, budget_s=12.0):
                       f"{el:.1f} s"}
 
 
+def serving_run(n, dev):
+    """Bounded continuous-batching run: a seeded Poisson stream of n cavity
+    and channel solves (sides 48..160, FP32 deviation storage, residual
+    target 1e-5 over 1000-step windows, cap 60,000 steps), served by
+    serve.Server; the same requests are then solved one at a time in FP64
+    with plain per-step launches (the sequential baseline)."""
+    from paper_1809_08683_gb300 import serve
+    mix = W.serving_mix(n=n, seed=1810, min_side=48, max_side=160, mean_interarrival=0.05,
+                        tol=1e-5, max_steps=60000, precision=1)
+    reqs = [serve.Request(rid=m["rid"], cfg=m["cfg"], arrival=m["arrival"], tol=m["tol"],
+                          max_steps=m["max_steps"]) for m in mix]
+    srv = serve.Server(max_slots=64, chunk=1000, graph_steps=100)
+    srv.run(reqs)
+    lat = [r.latency for r in reqs]
+    served = {"requests": n, "wall_s": srv.wall, "mlups": srv.node_steps / srv.wall / 1e6,
+              **{k + "_latency_s": v for k, v in serve.percentiles(lat).items()},
+              "converged": sum(r.status == "converged" for r in reqs),
+              "capped": sum(r.status == "capped" for r in reqs),
+              "unstable": sum(r.status == "unstable" for r in reqs)}
+    seq_reqs = []
+    t0 = time.perf_counter()
+    node_steps = 0
+    for m in mix:
+        c = dict(m["cfg"])
+        c["precision"] = 0
+        r = serve.Request(rid=m["rid"], cfg=c, tol=m["tol"], max_steps=m["max_steps"])
+        serve.solve_sequential(r)
+        node_steps += r.steps * r.nodes
+        seq_reqs.append(r)
+    seq_wall = time.perf_counter() - t0
+    solve = [r.result.get("solve_s") for r in seq_reqs]
+    served["sequential_fp64"] = {"wall_s": seq_wall, "mlups": node_steps / seq_wall / 1e6,
+                                 **{k + "_solve_s": v for k, v in serve.percentiles(solve).items()}}
+    served["speedup_vs_sequential_fp64"] = seq_wall / srv.wall
+    served["mix"] = "config-5 style Poisson stream (mean 50 ms), cavities and channels, sides 48..160, seed 1810"
+    return served
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -213,6 +254,10 @@ def main():
     chunk = args.chunk or chunk
     stream = torch.cuda.Stream(device=dev)
     lats = [lbm.Lattice(c, stream=stream, device=dev) for c in cfgs]
+    if args.tile:
+        t = [int(v) for v in args.tile.split(",")]
+        for lat in lats:
+            lat.set_tile(t[0], t[1], t[2] if len(t) > 2 else 0)
     batch = lbm.Batch(lats, graph_steps=0)
     nodes = sum(c["nx"] * c["ny"] for c in cfgs)
     prec = int(cfgs[0].get("precision", 0))
@@ -288,6 +333,15 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(cfgs)
 
+    serving = None
+    if rank == 0 and args.serving > 0:
+        batch.close()
+        for lat in lats:
+            lat.close()
+        lats, batch = [], None
+        torch.cuda.empty_cache()
+        serving = serving_run(args.serving, dev)
+
     if rank == 0:
         desc = dict(desc)
         desc.update({"nodes": nodes, "time_steps_per_bench_step": chunk,
@@ -302,9 +356,11 @@ def main():
                          "kernel": "k_collide_stream", "alg_bytes_per_launch": alg_bytes,
                          "avg_launch_ms": avg_collide_ms, "wall_pass_ms_per_step": t_wall / steps_total},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clocks,
+            "serving": serving,
         }
         print(json.dumps(out))
-    batch.close()
+    if batch is not None:
+        batch.close()
     for lat in lats:
         lat.close()
     if world > 1:

@@ -140,9 +140,18 @@ lbm_status lbm_init_macros(lbm_ctx* ctx, const double* rho, const double* ux,
 /* Derived constants: R, Cv, Cp, mu0, p0, eta0, lambda0, c_s^2. */
 lbm_status lbm_derived(const lbm_ctx* ctx, double* out8);
 
-/* Launch shape of the fused kernel: strip width bx (32, 64 or 128 threads,
- * one CTA per strip) and rows per CTA by (>= 1).  Used by the autotuner. */
-lbm_status lbm_set_tile(lbm_ctx* ctx, int bx, int by);
+/* Launch shape of the fused kernel: one CTA per strip of bx columns and by
+ * rows (>= 1).  pair = 0: one node per thread, bx = 32, 64 or 128.
+ * pair = 1 or 2 (FP32 storage only): two neighbouring nodes per thread in
+ * packed FP32 arithmetic, bx = 64, 128 or 256; pair = 1 keeps each node's
+ * macros in registers between the row pass and the collision, pair = 2
+ * recomputes them (fewer registers, more threads per SM).  pair = 3 (FP32
+ * storage only): one node per thread, bx = 32, 64 or 128, recomputing the
+ * macros.  pair = 0 shapes of any width give identical results; pair 1-3
+ * agree with them to FP32 rounding (their arithmetic is contracted
+ * differently).
+ * Used by the autotuner. */
+lbm_status lbm_set_tile(lbm_ctx* ctx, int bx, int by, int pair);
 
 /* Steps taken since the last (re)initialisation. */
 long lbm_step_count(const lbm_ctx* ctx);

@@ -52,22 +52,31 @@ def _store(d):
     os.replace(tmp, _CACHE_PATH)
 
 
+PAIR_BX_CANDIDATES = (64, 128, 256)
+
+
 def candidates(cfg: dict):
+    """(bx, by, pair) shapes worth timing for this lattice: one node per
+    thread for every precision, two nodes per thread for FP32 storage."""
+    shapes = [(bx, 0) for bx in BX_CANDIDATES]
+    if int(cfg.get("precision", 0)) == 1:
+        shapes += [(bx, 3) for bx in BX_CANDIDATES]
+        shapes += [(bx, pr) for bx in PAIR_BX_CANDIDATES for pr in (1, 2)]
     out = []
-    for bx in BX_CANDIDATES:
+    for bx, pr in shapes:
         if bx > 32 and cfg["nx"] <= bx // 2:
             continue
         for by in BY_CANDIDATES:
             if by > cfg["ny"] and by != BY_CANDIDATES[0]:
                 continue
-            out.append((bx, by))
+            out.append((bx, by, pr))
     return out
 
 
-def measure(cfg: dict, bx: int, by: int, steps: int = 20, stream=None) -> float:
+def measure(cfg: dict, bx: int, by: int, pair: int = 0, steps: int = 20, stream=None) -> float:
     """MLUPS of the fused kernel alone for one launch shape."""
     lat = lbm.Lattice(cfg, stream=stream)
-    lat.set_tile(bx, by)
+    lat.set_tile(bx, by, pair)
     batch = lbm.Batch([lat], graph_steps=0)
     batch.step_profiled(4)                       # warm-up
     ms, _ = batch.step_profiled(steps)
@@ -77,20 +86,20 @@ def measure(cfg: dict, bx: int, by: int, steps: int = 20, stream=None) -> float:
 
 
 def tune(cfg: dict, steps: int = 20, force: bool = False, stream=None) -> tuple:
-    """Best (bx, by) for this configuration's class, measured on first use."""
+    """Best (bx, by, pair) for this configuration's class, measured on first use."""
     key = key_for(cfg)
     with _lock:
         cache = _load()
-        if key in cache and not force:
+        if key in cache and not force and len(cache[key]["tile"]) == 3:
             return tuple(cache[key]["tile"])
     results = {}
-    for bx, by in candidates(cfg):
-        results[(bx, by)] = measure(cfg, bx, by, steps, stream)
+    for bx, by, pr in candidates(cfg):
+        results[(bx, by, pr)] = measure(cfg, bx, by, pr, steps, stream)
     best = max(results, key=results.get)
     with _lock:
         cache = _load()
         cache[key] = {"tile": list(best), "mlups": results[best],
-                      "all": {f"{b[0]}x{b[1]}": v for b, v in results.items()}}
+                      "all": {f"{b[0]}x{b[1]}{'p' if b[2] else ''}": v for b, v in results.items()}}
         _store(cache)
     return best
 
@@ -98,5 +107,5 @@ def tune(cfg: dict, steps: int = 20, force: bool = False, stream=None) -> tuple:
 def apply(lattices, steps: int = 20):
     """Set every lattice's launch shape from the cache, tuning unseen classes."""
     for lat in lattices:
-        bx, by = tune(lat.cfg, steps=steps, stream=lat.stream)
-        lat.set_tile(bx, by)
+        bx, by, pr = tune(lat.cfg, steps=steps, stream=lat.stream)
+        lat.set_tile(bx, by, pr)

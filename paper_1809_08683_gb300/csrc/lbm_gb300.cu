@@ -28,8 +28,10 @@
 #include <vector>
 
 #include "../../include/lbm.h"
+#include "lbm_f2.cuh"
 #include "lbm_node.cuh"
 
+using lbm::f2;
 using lbm::Mac;
 using lbm::Params;
 
@@ -232,12 +234,16 @@ template <typename R, int BX>
 struct FusedTraits {
     static constexpr int S = BX == 32 ? 3 : 4;
     static constexpr int MINB = (sizeof(R) == 4 ? 512 : 256) / BX;
+    static constexpr int MINB_LEAN = (sizeof(R) == 4 ? 640 : 256) / BX;  // about 100 registers in FP32
 };
 
-template <typename R, int BX, int S>
-__global__ void __launch_bounds__(BX, FusedTraits<R, BX>::MINB) k_collide_stream(const Work* __restrict__ work,
-                                                       InstDesc* const* __restrict__ descs, int step_par,
-                                                       const long long* __restrict__ counter) {
+// KEEP = true carries each thread's macros from the row pass to the
+// collision; KEEP = false recomputes them from the staged DFs, trading about
+// 50 instructions per node for fewer registers and more resident warps.
+template <typename R, int BX, int S, bool KEEP = true>
+__global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTraits<R, BX>::MINB_LEAN)
+    k_collide_stream(const Work* __restrict__ work, InstDesc* const* __restrict__ descs, int step_par,
+                     const long long* __restrict__ counter) {
     using L = FusedSmem<R, BX, S>;
     constexpr int E = L::E, W = L::W;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -371,7 +377,7 @@ __global__ void __launch_bounds__(BX, FusedTraits<R, BX>::MINB) k_collide_stream
         issue(k + S);  // stage of logical row k is free: its collision finished before the barrier
 
         if (active) {
-            if (!(isfinite(mc.rho_d) && isfinite(mc.T_d))) atomicOr(status, 1u);
+            if (KEEP && !(isfinite(mc.rho_d) && isfinite(mc.T_d))) atomicOr(status, 1u);
             const int sm = k & 3, s0 = (k + 1) & 3, sp = (k + 2) & 3;
             const bool onS = !py && j == 0, onN = !py && j == ny - 1;
             const bool onW = !px && x == 0, onE = !px && x == nx - 1;
@@ -420,6 +426,10 @@ __global__ void __launch_bounds__(BX, FusedTraits<R, BX>::MINB) k_collide_stream
             const R* st = stage + (size_t)((k + 1) % S) * 18 * W + E + tid;
 #pragma unroll
             for (int q = 0; q < 18; ++q) v[q] = st[q * W];
+            if (!KEEP) {
+                node_macros(P, v, mc);
+                if (!(isfinite(mc.rho_d) && isfinite(mc.T_d))) atomicOr(status, 1u);
+            }
             AddDither add{mix32(step_hash ^ ((uint32_t)j * 0x85ebca77u + (uint32_t)x * 0xc2b2ae3du))};
             lbm::collide(P, mc, v, v + 9, grx, gry, gpx, gpy, add);
 
@@ -458,10 +468,335 @@ __global__ void __launch_bounds__(BX, FusedTraits<R, BX>::MINB) k_collide_stream
                 }
             }
         }
-        mc = mn;
+        if (KEEP) mc = mn;
     }
     if (s_abort && tid == 0) {
         // leave no bulk copy in flight into this CTA's shared memory
+        for (int l = 0; l <= last_l; ++l)
+            if (phys(l) >= 0) mbar_wait(&bars[l % S], (uint32_t)((l / S) & 1));
+    }
+}
+
+// ------------------------------------------------------------------------
+// fused collide + stream, two nodes per thread in packed FP32
+// ------------------------------------------------------------------------
+
+// Packed-pair variant of the FP32 fused kernel: thread t owns the columns
+// x0 + 2t and x0 + 2t + 1 of its strip and evaluates the node arithmetic
+// once for both, in packed FP32 (lbm_f2.cuh).  Row staging, the macro ring and
+// the push are those of k_collide_stream; shared-memory loads are 8-byte
+// pairs, and populations that stream along y only are stored as pairs.
+template <int BX>
+struct PairSmem {
+    static constexpr int S = 4;
+    static constexpr int E = 4;              // floats per 16-byte halo chunk
+    static constexpr int W = BX + 2 * E;
+    static constexpr int RW = BX + 4;        // ring row: x - x0 + 2, halos at 1 and (xlast - x0) + 3
+    static constexpr size_t stage_bytes = (size_t)18 * W * sizeof(float);
+    static constexpr size_t off_bars = (size_t)S * stage_bytes;
+    static constexpr size_t off_p2 = (off_bars + 8 * S + 15) / 16 * 16;
+    static constexpr size_t off_p1 = (off_p2 + sizeof(Params<f2>) + 15) / 16 * 16;
+    static constexpr size_t off_ring = (off_p1 + sizeof(Params<float>) + 15) / 16 * 16;
+    static constexpr size_t bytes = off_ring + (size_t)2 * 4 * RW * sizeof(float);
+};
+
+__device__ void broadcast_params(const Params<float>& a, Params<f2>& b) {
+#define BP(f) b.f = f2(a.f)
+    BP(rho0); BP(T0); BP(E0); BP(Cv); BP(inv_Cv); BP(Rg); BP(eos_a); BP(eos_b); BP(p0); BP(rho0E0_p0);
+    BP(rho0Cp0); BP(mu0); BP(inv_T0); BP(visc_S); BP(lam_fac); BP(tj_fac); BP(e_fac); BP(alpha1);
+    BP(beta1); BP(alpha2); BP(beta2); BP(kk); BP(hh); BP(bb); BP(gamma1); BP(gamma2); BP(cR11);
+    BP(cR17); BP(cR18); BP(cR71); BP(cR77); BP(cR81); BP(cR88); BP(Fx); BP(Fy); BP(cs_b0);
+#undef BP
+    b.eos = a.eos;
+    b.visc = a.visc;
+    b.force_mode = a.force_mode;
+    b.corrections = a.corrections;
+}
+
+// Stochastic rounding of a pair of nodes: one draw per node and link.
+struct AddDither2 {
+    mutable uint32_t h;
+    __device__ __forceinline__ void operator()(f2& f, f2 df, f2& g, f2 dg) const {
+        h = h * 1664525u + 1013904223u;
+        const uint32_t h2 = h * 1664525u + 1013904223u;
+        h = h2;
+        const float2 r = make_float2(__int_as_float(0x3f800000u | (h >> 9)) - 1.5f,
+                                     __int_as_float(0x3f800000u | (h2 << 9 >> 9)) - 1.5f);
+        const float2 k = make_float2(1.1920928955078125e-7f, 1.1920928955078125e-7f);
+        const float2 uf = __fmul2_rn(make_float2(__int_as_float(__float_as_int(f.v.x) & 0x7f800000),
+                                                 __int_as_float(__float_as_int(f.v.y) & 0x7f800000)), k);
+        const float2 ug = __fmul2_rn(make_float2(__int_as_float(__float_as_int(g.v.x) & 0x7f800000),
+                                                 __int_as_float(__float_as_int(g.v.y) & 0x7f800000)), k);
+        f = f2(__fadd2_rn(f.v, __ffma2_rn(r, uf, df.v)));
+        g = f2(__fadd2_rn(g.v, __ffma2_rn(r, ug, dg.v)));
+    }
+};
+
+// KEEP = true carries each thread's macros from the row pass to the
+// collision (more registers); KEEP = false recomputes them from the staged
+// DFs at collision time, which lets two nodes per thread fit 128 registers.
+template <int BX, bool KEEP>
+__global__ void __launch_bounds__(BX / 2, (KEEP ? 512 : 768) / BX) k_collide_pair(const Work* __restrict__ work,
+                                                                    InstDesc* const* __restrict__ descs,
+                                                                    int step_par, const long long* __restrict__ counter) {
+    using L = PairSmem<BX>;
+    constexpr int E = L::E, W = L::W, S = L::S, RW = L::RW;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float* stage = reinterpret_cast<float*>(smem);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::off_bars);
+    Params<f2>& P2 = *reinterpret_cast<Params<f2>*>(smem + L::off_p2);
+    Params<float>& P1 = *reinterpret_cast<Params<float>*>(smem + L::off_p1);
+    float(*s_rho)[RW] = reinterpret_cast<float(*)[RW]>(smem + L::off_ring);
+    float(*s_p)[RW] = s_rho + 4;
+    __shared__ int s_abort;
+
+    const Work w = work[blockIdx.x];
+    const InstDesc* D = descs[w.inst];
+    load_params(&P1, &D->pf);
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int k = 0; k < S; ++k) mbar_init(&bars[k], 1);
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    const int nx = D->nx, ny = D->ny, pitch = D->pitch, px = D->px, py = D->py;
+    const long long plane = D->plane;
+    const int b = w.par ^ step_par;
+    const float* __restrict__ src = reinterpret_cast<const float*>(D->buf[b]);
+    float* __restrict__ dst = reinterpret_cast<float*>(D->buf[b ^ 1]);
+    unsigned int* status = D->status;
+    const uint32_t step_hash = mix32((uint32_t)(w.step0 + *counter) * 0x9e3779b1u + 0x632be5abu);
+    __syncthreads();
+    if (tid == 0) broadcast_params(P1, P2);
+    __syncthreads();
+
+    const int xa = w.x0 + 2 * tid, xb = xa + 1;
+    const bool act_a = xa < nx, act_b = xb < nx;
+    const int xlast = min(w.x0 + BX, nx) - 1;
+    const int towner = (xlast - w.x0) >> 1;  // thread that owns the last column
+    int xhl = w.x0 - 1;
+    bool has_l = true;
+    if (xhl < 0) { if (px) xhl = nx - 1; else has_l = false; }
+    int xhr = xlast + 1;
+    bool has_r = true;
+    if (xhr >= nx) { if (px) xhr = 0; else has_r = false; }
+    const int xcl = has_l ? (xhl / E) * E : 0, xcr = has_r ? (xhr / E) * E : 0;
+    const int nmain = min(BX, pitch - w.x0);
+    const int nrows = w.y1 - w.y0;
+    const int last_l = nrows + 1;
+    const int ca = 2 * tid + 2;                 // ring column of x_a
+    const int cr = (xlast - w.x0) + 3;          // ring column of the right halo
+
+    auto phys = [&](int l) -> int {
+        int y = w.y0 - 1 + l;
+        if (y < 0 || y >= ny) {
+            if (!py) return -1;
+            y = (y < 0) ? y + ny : y - ny;
+        }
+        return y;
+    };
+
+    auto issue = [&](int l) {
+        if (l > last_l || tid >= 32) return;
+        const int s = l % S;
+        const int y = phys(l);
+        if (tid == 0) {
+            if (y < 0) mbar_arrive(&bars[s]);
+            else mbar_arrive_expect_tx(&bars[s], (uint32_t)(18 * (nmain * 4 + 16 * (has_l + has_r))));
+        }
+        __syncwarp();
+        if (y >= 0 && tid < 18) {
+            fence_proxy_async();
+            const float* row = src + tid * plane + (long long)y * pitch;
+            float* st = stage + (size_t)s * 18 * W + (size_t)tid * W;
+            bulk_g2s(st + E, row + w.x0, (uint32_t)(nmain * 4), &bars[s]);
+            if (has_l) bulk_g2s(st, row + xcl, 16u, &bars[s]);
+            if (has_r) bulk_g2s(st + E + BX, row + xcr, 16u, &bars[s]);
+        }
+    };
+
+    auto row_macros = [&](int l, Mac<f2>& m) -> bool {
+        const int s = l % S;
+        if (!mbar_wait(&bars[s], (uint32_t)((l / S) & 1))) {
+            atomicOr(status, 2u);
+            s_abort = 1;
+            return false;
+        }
+        const float* st = stage + (size_t)s * 18 * W;
+        const int slot = l & 3;
+        if (act_a) {
+            f2 v[18];
+#pragma unroll
+            for (int q = 0; q < 18; ++q) v[q] = f2(*reinterpret_cast<const float2*>(st + q * W + E + 2 * tid));
+            f2 rd, jx, jy, sg;
+            lbm::node_sums(v, v + 9, rd, jx, jy, sg);
+            lbm::macros(P2, rd, jx, jy, sg, m);
+            *reinterpret_cast<float2*>(&s_rho[slot][ca]) = m.rho_d.v;
+            *reinterpret_cast<float2*>(&s_p[slot][ca]) = m.p_d.v;
+        }
+        const bool hl = (tid == 0 && has_l), hr = (tid == towner && has_r);
+        if (hl || hr) {
+            // halo columns in scalar arithmetic, after this thread's own pair
+            float v[18];
+            Mac<float> h;
+            if (hl) {
+#pragma unroll
+                for (int q = 0; q < 18; ++q) v[q] = st[q * W + (xhl - xcl)];
+                node_macros(P1, v, h);
+                s_rho[slot][1] = h.rho_d;
+                s_p[slot][1] = h.p_d;
+            }
+            if (hr) {
+#pragma unroll
+                for (int q = 0; q < 18; ++q) v[q] = st[q * W + E + BX + (xhr - xcr)];
+                node_macros(P1, v, h);
+                s_rho[slot][cr] = h.rho_d;
+                s_p[slot][cr] = h.p_d;
+            }
+        }
+        return true;
+    };
+
+    for (int l = 0; l < S; ++l) issue(l);
+    Mac<f2> mc, mn;
+    if (phys(0) >= 0) row_macros(0, mn);
+    row_macros(1, mc);
+
+    for (int k = 0; k < nrows; ++k) {
+        const int j = w.y0 + k;
+        if (phys(k + 2) >= 0) row_macros(k + 2, mn);
+        __syncthreads();
+        if (s_abort) break;
+        issue(k + S);
+
+        if (act_a) {
+            if (KEEP && !(isfinite(mc.rho_d.v.x) && isfinite(mc.T_d.v.x) && isfinite(mc.rho_d.v.y) && isfinite(mc.T_d.v.y)))
+                atomicOr(status, act_b ? 1u : ((isfinite(mc.rho_d.v.x) && isfinite(mc.T_d.v.x)) ? 0u : 1u));
+            const int sm = k & 3, s0 = (k + 1) & 3, sp = (k + 2) & 3;
+            // interior stencil for both nodes: columns (ca-1, ca) on the left, (ca+1, ca+2) on the right
+            auto grad = [&](float (*a)[RW], f2& gx, f2& gy) {
+                const float2 cm = *reinterpret_cast<const float2*>(&a[sm][ca]);
+                const float2 c0 = *reinterpret_cast<const float2*>(&a[s0][ca]);
+                const float2 cp = *reinterpret_cast<const float2*>(&a[sp][ca]);
+                const f2 lm(make_float2(a[sm][ca - 1], cm.x)), rm(make_float2(cm.y, a[sm][ca + 2]));
+                const f2 l0(make_float2(a[s0][ca - 1], c0.x)), r0(make_float2(c0.y, a[s0][ca + 2]));
+                const f2 lp(make_float2(a[sp][ca - 1], cp.x)), rp(make_float2(cp.y, a[sp][ca + 2]));
+                const f2 t(1.0f / 3.0f), d(1.0f / 12.0f);
+                gx = t * (r0 - l0) + d * ((rp - lp) + (rm - lm));
+                gy = t * (f2(cp) - f2(cm)) + d * ((rp - rm) + (lp - lm));
+            };
+            f2 grx, gry, gpx, gpy;
+            grad(s_rho, grx, gry);
+            grad(s_p, gpx, gpy);
+            const bool rowwall = !py && (j == 0 || j == ny - 1);
+            const bool colwall = !px && (xa == 0 || xb >= nx - 1);
+            if (rowwall || colwall) {
+                // wall nodes: one-sided second order along the inward normal,
+                // central along the wall (scalar, per node of the pair)
+#pragma unroll
+                for (int lane = 0; lane < 2; ++lane) {
+                    const int x = lane ? xb : xa;
+                    if (lane && !act_b) break;
+                    const int c = ca + lane;
+                    const bool onS = !py && j == 0, onN = !py && j == ny - 1;
+                    const bool onW = !px && x == 0, onE = !px && x == nx - 1;
+                    if (!(onS || onN || onW || onE)) continue;
+                    float gr[4];
+                    for (int fld = 0; fld < 2; ++fld) {
+                        float (*a)[RW] = fld ? s_p : s_rho;
+                        const float v0 = a[s0][c];
+                        float gxs, gys;
+                        if (onW || onE) {
+                            const int dx = onW ? 1 : -1;
+                            float r2, p2;
+                            rho_p_at(P1, src, plane, pitch, x + 2 * dx, j, r2, p2);
+                            gxs = (float)dx * (-3.0f * v0 + 4.0f * a[s0][c + dx] - (fld ? p2 : r2)) * 0.5f;
+                        } else {
+                            gxs = (a[s0][c + 1] - a[s0][c - 1]) * 0.5f;
+                        }
+                        if (onS || onN) {
+                            const int dy = onS ? 1 : -1;
+                            float r2, p2;
+                            rho_p_at(P1, src, plane, pitch, x, j + 2 * dy, r2, p2);
+                            const float v1 = onS ? a[sp][c] : a[sm][c];
+                            gys = (float)dy * (-3.0f * v0 + 4.0f * v1 - (fld ? p2 : r2)) * 0.5f;
+                        } else {
+                            gys = (a[sp][c] - a[sm][c]) * 0.5f;
+                        }
+                        gr[2 * fld] = gxs;
+                        gr[2 * fld + 1] = gys;
+                    }
+                    if (lane) { grx.v.y = gr[0]; gry.v.y = gr[1]; gpx.v.y = gr[2]; gpy.v.y = gr[3]; }
+                    else { grx.v.x = gr[0]; gry.v.x = gr[1]; gpx.v.x = gr[2]; gpy.v.x = gr[3]; }
+                }
+            }
+
+            f2 v[18];
+            const float* st = stage + (size_t)((k + 1) % S) * 18 * W + E + 2 * tid;
+#pragma unroll
+            for (int q = 0; q < 18; ++q) v[q] = f2(*reinterpret_cast<const float2*>(st + q * W));
+            if (!KEEP) {
+                f2 rd, jx, jy, sg;
+                lbm::node_sums(v, v + 9, rd, jx, jy, sg);
+                lbm::macros(P2, rd, jx, jy, sg, mc);
+            }
+            if (!KEEP && !(isfinite(mc.rho_d.v.x) && isfinite(mc.T_d.v.x) && (!act_b || (isfinite(mc.rho_d.v.y) && isfinite(mc.T_d.v.y)))))
+                atomicOr(status, 1u);
+            AddDither2 add{mix32(step_hash ^ ((uint32_t)j * 0x85ebca77u + (uint32_t)xa * 0xc2b2ae3du))};
+            lbm::collide(P2, mc, v, v + 9, grx, gry, gpx, gpy, add);
+
+            if (act_b && xa >= 1 && xb <= nx - 2 && j >= 1 && j <= ny - 2) {
+                // both nodes interior: no wrap, no bounce-back
+                float* o = dst + ((long long)j * pitch + xa);
+                const int pl = (int)plane;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const int ex = (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+                    const int ey = (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+                    const int off = ey * pitch + ex;
+                    if (ex == 0) {
+                        *reinterpret_cast<float2*>(o + i * pl + off) = v[i].v;
+                        *reinterpret_cast<float2*>(o + (9 + i) * pl + off) = v[9 + i].v;
+                    } else {
+                        o[i * pl + off] = v[i].v.x;
+                        o[i * pl + off + 1] = v[i].v.y;
+                        o[(9 + i) * pl + off] = v[9 + i].v.x;
+                        o[(9 + i) * pl + off + 1] = v[9 + i].v.y;
+                    }
+                }
+            } else {
+                // edge pair: per node, periodic wrap or bounce-back into its own slot
+#pragma unroll
+                for (int lane = 0; lane < 2; ++lane) {
+                    if (lane && !act_b) break;
+                    const int x = lane ? xb : xa;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        const int ex = (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+                        const int ey = (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+                        const int opp = (i == 0) ? 0 : (i <= 4 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5);
+                        const float fv = lane ? v[i].v.y : v[i].v.x;
+                        const float gv = lane ? v[9 + i].v.y : v[9 + i].v.x;
+                        int xd = x + ex, yd = j + ey;
+                        bool out = false;
+                        if (xd < 0 || xd >= nx) { if (px) xd = (xd < 0) ? nx - 1 : 0; else out = true; }
+                        if (yd < 0 || yd >= ny) { if (py) yd = (yd < 0) ? ny - 1 : 0; else out = true; }
+                        if (out) {
+                            const long long t2 = (long long)j * pitch + x;
+                            dst[opp * plane + t2] = fv;
+                            dst[(9 + opp) * plane + t2] = gv;
+                        } else {
+                            const long long t2 = (long long)yd * pitch + xd;
+                            dst[i * plane + t2] = fv;
+                            dst[(9 + i) * plane + t2] = gv;
+                        }
+                    }
+                }
+            }
+        }
+        if (KEEP) mc = mn;
+    }
+    if (s_abort && tid == 0) {
         for (int l = 0; l <= last_l; ++l)
             if (phys(l) >= 0) mbar_wait(&bars[l % S], (uint32_t)((l / S) & 1));
     }
@@ -976,7 +1311,7 @@ struct lbm_ctx {
     double* d_snap = nullptr;
     double* d_stage = nullptr;
     Work* d_work = nullptr;
-    int n_work = 0, bx = 128, by = 0;
+    int n_work = 0, bx = 128, by = 0, pair = 0;
     BWork* d_bwork = nullptr;
     int n_bwork = 0;
     long steps = 0;
@@ -995,7 +1330,7 @@ struct lbm_batch {
     Work* d_work = nullptr;
     BWork* d_bwork = nullptr;
     // launch groups: [precision][bx index] ranges of d_work; [precision] ranges of d_bwork
-    int w_off[2][3] = {{0, 0, 0}, {0, 0, 0}}, w_cnt[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    int w_off[2][12] = {{0}}, w_cnt[2][12] = {{0}};
     int b_off[2] = {0, 0}, b_cnt[2] = {0, 0};
     long steps = 0;
     int graph_steps = 0;
@@ -1050,7 +1385,7 @@ void ensure_tick(std::vector<BWork>& v, int inst, int par) {
 int default_rows(const lbm_config& c, int bx) {
     // enough CTAs to cover 152 SMs several times, runs of at most 64 rows
     const long long strips = (c.nx + bx - 1) / bx;
-    long long by = 64;
+    long long by = 32;
     while (by > 4 && strips * ((c.ny + by - 1) / by) < 4 * 152) by /= 2;
     return (int)std::max<long long>(1, std::min<long long>(by, c.ny));
 }
@@ -1065,14 +1400,23 @@ lbm_status upload_work(lbm_ctx* c) {
     return LBM_OK;
 }
 
-template <typename R, int BX>
+template <typename R, int BX, bool KEEP = true>
 cudaError_t configure_collide() {
     constexpr int S = FusedTraits<R, BX>::S;
-    cudaError_t e = cudaFuncSetAttribute(k_collide_stream<R, BX, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_collide_stream<R, BX, S, KEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)FusedSmem<R, BX, S>::bytes);
     if (e != cudaSuccess) return e;
     // prefer shared memory over L1: the row stages, not L1, feed the kernel
-    return cudaFuncSetAttribute(k_collide_stream<R, BX, S>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    return cudaFuncSetAttribute(k_collide_stream<R, BX, S, KEEP>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared);
+}
+
+template <int BX, bool KEEP>
+cudaError_t configure_pair() {
+    cudaError_t e = cudaFuncSetAttribute(k_collide_pair<BX, KEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)PairSmem<BX>::bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_collide_pair<BX, KEEP>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                 (int)cudaSharedmemCarveoutMaxShared);
 }
 
@@ -1084,6 +1428,15 @@ lbm_status configure_kernels() {
     cudaError_t e = configure_collide<float, 32>();
     if (e == cudaSuccess) e = configure_collide<float, 64>();
     if (e == cudaSuccess) e = configure_collide<float, 128>();
+    if (e == cudaSuccess) e = configure_collide<float, 32, false>();
+    if (e == cudaSuccess) e = configure_collide<float, 64, false>();
+    if (e == cudaSuccess) e = configure_collide<float, 128, false>();
+    if (e == cudaSuccess) e = configure_pair<64, true>();
+    if (e == cudaSuccess) e = configure_pair<128, true>();
+    if (e == cudaSuccess) e = configure_pair<256, true>();
+    if (e == cudaSuccess) e = configure_pair<64, false>();
+    if (e == cudaSuccess) e = configure_pair<128, false>();
+    if (e == cudaSuccess) e = configure_pair<256, false>();
     if (e == cudaSuccess) e = configure_collide<double, 32>();
     if (e == cudaSuccess) e = configure_collide<double, 64>();
     if (e == cudaSuccess) e = configure_collide<double, 128>();
@@ -1092,20 +1445,53 @@ lbm_status configure_kernels() {
     return LBM_OK;
 }
 
-template <typename R, int BX>
+template <typename R, int BX, bool KEEP = true>
 void launch_collide_bx(const Work* work, int n, InstDesc* const* descs, int par, const long long* counter,
                        cudaStream_t s) {
     constexpr int S = FusedTraits<R, BX>::S;
-    k_collide_stream<R, BX, S><<<n, BX, FusedSmem<R, BX, S>::bytes, s>>>(work, descs, par, counter);
+    k_collide_stream<R, BX, S, KEEP><<<n, BX, FusedSmem<R, BX, S>::bytes, s>>>(work, descs, par, counter);
+}
+
+template <int BX, bool KEEP>
+void launch_pair_bx(const Work* work, int n, InstDesc* const* descs, int par, const long long* counter,
+                    cudaStream_t s) {
+    k_collide_pair<BX, KEEP><<<n, BX / 2, PairSmem<BX>::bytes, s>>>(work, descs, par, counter);
+}
+
+// Fused-kernel variants: strips of 32, 64, 128 columns, one node per thread
+// (indices 0-2, pair = 0); strips of 64, 128, 256 columns, two nodes per
+// thread in packed FP32 keeping the row macros in registers (indices 3-5,
+// pair = 1) or recomputing them at collision time (indices 6-8, pair = 2);
+// one node per thread recomputing the macros, fewer registers (indices 9-11,
+// pair = 3).  Variants 3-11 need FP32 storage.
+constexpr int kVariants = 12;
+static const int kVariantWidth[kVariants] = {32, 64, 128, 64, 128, 256, 64, 128, 256, 32, 64, 128};
+static const int kVariantPair[kVariants] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3};
+
+int variant_index(int bx, int pair) {
+    for (int v = 0; v < kVariants; ++v)
+        if (kVariantWidth[v] == bx && kVariantPair[v] == pair) return v;
+    return -1;
 }
 
 template <typename R>
-void launch_collide(const Work* work, int n, int bx, InstDesc* const* descs, int par, const long long* counter,
+void launch_collide(const Work* work, int n, int variant, InstDesc* const* descs, int par, const long long* counter,
                     cudaStream_t s) {
     if (n <= 0) return;
-    if (bx == 32) launch_collide_bx<R, 32>(work, n, descs, par, counter, s);
-    else if (bx == 64) launch_collide_bx<R, 64>(work, n, descs, par, counter, s);
-    else launch_collide_bx<R, 128>(work, n, descs, par, counter, s);
+    switch (variant) {
+    case 0: launch_collide_bx<R, 32>(work, n, descs, par, counter, s); break;
+    case 1: launch_collide_bx<R, 64>(work, n, descs, par, counter, s); break;
+    case 3: launch_pair_bx<64, true>(work, n, descs, par, counter, s); break;
+    case 4: launch_pair_bx<128, true>(work, n, descs, par, counter, s); break;
+    case 5: launch_pair_bx<256, true>(work, n, descs, par, counter, s); break;
+    case 6: launch_pair_bx<64, false>(work, n, descs, par, counter, s); break;
+    case 7: launch_pair_bx<128, false>(work, n, descs, par, counter, s); break;
+    case 8: launch_pair_bx<256, false>(work, n, descs, par, counter, s); break;
+    case 9: launch_collide_bx<R, 32, false>(work, n, descs, par, counter, s); break;
+    case 10: launch_collide_bx<R, 64, false>(work, n, descs, par, counter, s); break;
+    case 11: launch_collide_bx<R, 128, false>(work, n, descs, par, counter, s); break;
+    default: launch_collide_bx<R, 128>(work, n, descs, par, counter, s); break;
+    }
 }
 
 template <typename R>
@@ -1374,11 +1760,15 @@ lbm_status lbm_derived(const lbm_ctx* c, double* out8) {
     return LBM_OK;
 }
 
-lbm_status lbm_set_tile(lbm_ctx* c, int bx, int by) {
+lbm_status lbm_set_tile(lbm_ctx* c, int bx, int by, int pair) {
     if (!c) return fail(LBM_EINVAL, "null ctx");
-    if (bx != 32 && bx != 64 && bx != 128) return fail(LBM_EINVAL, "bx must be 32, 64 or 128");
+    if (pair && c->cfg.precision != LBM_FP32_DEV) return fail(LBM_EINVAL, "paired packed-FP32 strips need FP32 storage");
+    if (variant_index(bx, pair) < 0)
+        return fail(LBM_EINVAL, pair ? "paired strips (pair 1 or 2) are 64, 128 or 256 columns"
+                                     : "bx must be 32, 64 or 128");
     if (by < 1) return fail(LBM_EINVAL, "by must be >= 1");
     c->bx = bx;
+    c->pair = pair;
     c->by = std::min(by, c->cfg.ny);
     lbm_status st = upload_work(c);
     if (st != LBM_OK) return st;
@@ -1398,10 +1788,10 @@ lbm_status lbm_step(lbm_ctx* c, long nsteps) {
     for (long s = 0; s < nsteps; ++s) {
         const int par = (int)((c->steps + s) & 1);
         if (is_fp32(c)) {
-            launch_collide<float>(c->d_work, c->n_work, c->bx, c->d_descs, par, c->d_counter, c->stream);
+            launch_collide<float>(c->d_work, c->n_work, variant_index(c->bx, c->pair), c->d_descs, par, c->d_counter, c->stream);
             launch_boundary<float>(c->d_bwork, c->n_bwork, c->d_descs, par, c->d_counter, c->stream);
         } else {
-            launch_collide<double>(c->d_work, c->n_work, c->bx, c->d_descs, par, c->d_counter, c->stream);
+            launch_collide<double>(c->d_work, c->n_work, variant_index(c->bx, 0), c->d_descs, par, c->d_counter, c->stream);
             launch_boundary<double>(c->d_bwork, c->n_bwork, c->d_descs, par, c->d_counter, c->stream);
         }
     }
@@ -1605,19 +1995,14 @@ lbm_status lbm_conserved_sums_static(const lbm_ctx* c, double* out4) {
 // batched stepping
 // ------------------------------------------------------------------------
 
-static const int kWidths[3] = {32, 64, 128};
-
-static int width_index(int bx) { return bx == 32 ? 0 : (bx == 64 ? 1 : 2); }
-
 static void batch_launch_collide(lbm_batch* b, int par) {
     for (int pr = 0; pr < 2; ++pr)
-        for (int bi = 0; bi < 3; ++bi) {
-            const int bx = kWidths[bi];
-            if (!b->w_cnt[pr][bi]) continue;
+        for (int vi = 0; vi < kVariants; ++vi) {
+            if (!b->w_cnt[pr][vi]) continue;
             if (pr)
-                launch_collide<float>(b->d_work + b->w_off[pr][bi], b->w_cnt[pr][bi], bx, b->d_descs, par, b->d_counter, b->stream);
+                launch_collide<float>(b->d_work + b->w_off[pr][vi], b->w_cnt[pr][vi], vi, b->d_descs, par, b->d_counter, b->stream);
             else
-                launch_collide<double>(b->d_work + b->w_off[pr][bi], b->w_cnt[pr][bi], bx, b->d_descs, par, b->d_counter, b->stream);
+                launch_collide<double>(b->d_work + b->w_off[pr][vi], b->w_cnt[pr][vi], vi, b->d_descs, par, b->d_counter, b->stream);
         }
 }
 
@@ -1649,7 +2034,7 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, int graph_steps, lbm_ba
     lbm_batch* b = new lbm_batch();
     b->stream = ctxs[0]->stream;
     std::vector<InstDesc*> descs;
-    std::vector<Work> groups[2][3];
+    std::vector<Work> groups[2][kVariants];
     std::vector<BWork> bgroups[2];
     for (int i = 0; i < n; ++i) {
         lbm_ctx* c = ctxs[i];
@@ -1659,7 +2044,7 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, int graph_steps, lbm_ba
         }
         b->ctxs.push_back(c);
         descs.push_back(c->d_desc);
-        const int pr = is_fp32(c) ? 1 : 0, bi = width_index(c->bx);
+        const int pr = is_fp32(c) ? 1 : 0, bi = variant_index(c->bx, c->pair);
         const int par = (int)(c->steps & 1);
         auto w = make_work(c->cfg, i, c->bx, c->by, par, c->steps);
         groups[pr][bi].insert(groups[pr][bi].end(), w.begin(), w.end());
@@ -1668,7 +2053,7 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, int graph_steps, lbm_ba
     }
     std::vector<Work> all;
     for (int pr = 0; pr < 2; ++pr)
-        for (int bi = 0; bi < 3; ++bi) {
+        for (int bi = 0; bi < kVariants; ++bi) {
             b->w_off[pr][bi] = (int)all.size();
             b->w_cnt[pr][bi] = (int)groups[pr][bi].size();
             all.insert(all.end(), groups[pr][bi].begin(), groups[pr][bi].end());

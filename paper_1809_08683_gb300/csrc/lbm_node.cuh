@@ -58,6 +58,23 @@ struct Mac {
     R rho_d, rho, ir, ux, uy, Fx, Fy, qe, rhoE_d, T_d, T, p_d, eta_d, rhoH;
 };
 
+// Carnahan-Starling deviation p - p0 with p = Z(e) rho R T, e = b rho / 4
+// (Eq. EOSs.3).  The density part is differenced in FP64 to avoid
+// cancellation when the arithmetic type is FP32.
+LBM_HD double cs_dev1(double b, double rho0, double Rg, double rho_d, double T, double T_d) {
+    double r = rho0 + rho_d;
+    double e = b * r / 4.0, e0 = b * rho0 / 4.0;
+    double z = (1.0 + e + e * e - e * e * e) / ((1.0 - e) * (1.0 - e) * (1.0 - e));
+    double z0 = (1.0 + e0 + e0 * e0 - e0 * e0 * e0) / ((1.0 - e0) * (1.0 - e0) * (1.0 - e0));
+    return Rg * ((z * r - z0 * rho0) * T + z0 * rho0 * T_d);
+}
+LBM_HD double cs_dev(double b, double rho0, double Rg, double rho_d, double T, double T_d) {
+    return cs_dev1(b, rho0, Rg, rho_d, T, T_d);
+}
+LBM_HD float cs_dev(float b, float rho0, float Rg, float rho_d, float T, float T_d) {
+    return (float)cs_dev1(b, rho0, Rg, rho_d, T, T_d);
+}
+
 // p_EOS(rho, T) - p0.
 template <typename R>
 LBM_HD R eos_dev(const Params<R>& P, R rho_d, R rho, R T_d, R T) {
@@ -66,17 +83,8 @@ LBM_HD R eos_dev(const Params<R>& P, R rho_d, R rho, R T_d, R T) {
         return P.Rg * P.T0 * rho_d;
     case EOS_IDEAL:
         return P.Rg * (rho_d * T + P.rho0 * T_d);
-    case EOS_CS: {
-        // Carnahan-Starling: p = Z(e) rho R T, e = b rho / 4 (Eq. EOSs.3).  The
-        // density part is differenced in FP64 to avoid cancellation in FP32.
-        double b = (double)P.eos_b;
-        double r = (double)P.rho0 + (double)rho_d, r0 = (double)P.rho0;
-        double e = b * r / 4.0, e0 = b * r0 / 4.0;
-        double z = (1.0 + e + e * e - e * e * e) / ((1.0 - e) * (1.0 - e) * (1.0 - e));
-        double z0 = (1.0 + e0 + e0 * e0 - e0 * e0 * e0) / ((1.0 - e0) * (1.0 - e0) * (1.0 - e0));
-        double phi_d = z * r - z0 * r0;
-        return (R)((double)P.Rg * (phi_d * (double)T + z0 * r0 * (double)T_d));
-    }
+    case EOS_CS:
+        return cs_dev(P.eos_b, P.rho0, P.Rg, rho_d, T, T_d);
     default: {
         // rho R T / (1 - b rho) - a rho^2, differenced exactly:
         // [rho T (1 - b rho0) - rho0 T0 (1 - b rho)] = rho_d T + rho0 T_d - b rho rho0 T_d

@@ -99,7 +99,7 @@ def load(path: str | None = None):
         L.lbm_set_state.argtypes = [vp, dp, dp]
         L.lbm_init_macros.argtypes = [vp, dp, dp, dp, dp]
         L.lbm_derived.argtypes = [vp, dp]
-        L.lbm_set_tile.argtypes = [vp, i, i]
+        L.lbm_set_tile.argtypes = [vp, i, i, i]
         L.lbm_step_count.argtypes = [vp]
         L.lbm_step_count.restype = C.c_long
         L.lbm_destroy.argtypes = [vp]
@@ -259,8 +259,8 @@ class Lattice:
         _check(self.L, self.L.lbm_derived(self.h, _ptr(a)))
         return dict(zip(("R", "Cv", "Cp", "mu0", "p0", "eta0", "lambda0", "cs2"), a.tolist()))
 
-    def set_tile(self, bx: int, by: int):
-        _check(self.L, self.L.lbm_set_tile(self.h, int(bx), int(by)))
+    def set_tile(self, bx: int, by: int, pair: int = 0):
+        _check(self.L, self.L.lbm_set_tile(self.h, int(bx), int(by), int(pair)))
 
     def conserved_sums_static(self, out):
         """Total mass, x and y momentum and sum of g into the device tensor

@@ -101,8 +101,11 @@ def sutherland_ratio(theta, S=SUTHERLAND_S_OVER_T0):
     return theta * math.sqrt(theta) * (1.0 + S) / (theta + S)
 
 
-def tau_for(N, Ra, eps, tau_min=0.65, dtau_cold=0.045, u_peak=0.065, u_peak_over_uref=0.32,
-            strat=0.15, Pr=0.71):
+COLD_MARGIN = {EOS_IDEAL: 0.05, EOS_CUBIC: 0.068}
+
+
+def tau_for(N, Ra, eps, tau_min=0.65, dtau_cold=None, u_peak=0.065, u_peak_over_uref=0.32,
+            strat=0.15, Pr=0.71, eos=EOS_IDEAL):
     """Relaxation time at (rho0, T0) for a heated cavity of side N, and the
     Rayleigh number actually run.
 
@@ -113,7 +116,12 @@ def tau_for(N, Ra, eps, tau_min=0.65, dtau_cold=0.045, u_peak=0.065, u_peak_over
     stratification 3 g L = 3 U_ref^2 / (Pr 2 eps) below strat.  tau0 is the
     lower bound; when it exceeds the upper bound (Ra too high for the
     lattice), Ra is lowered to the largest value that meets it.  The bounds
-    come from GPU stability scans of eps up to 0.6 with varsigma/nu = 4."""
+    come from GPU stability scans of eps up to 0.6 with varsigma/nu = 4 over
+    6e4 steps, with about 10% headroom: the cold-wall margin is 0.05 for the
+    ideal gas and 0.068 for the cubic EOS, whose cold, dense fluid has a
+    much smaller p / rho."""
+    if dtau_cold is None:
+        dtau_cold = COLD_MARGIN.get(eos, 0.068)
     L = N - 1
     Tc = 1.0 - eps
     lo = max(tau_min, 0.5 + dtau_cold / (sutherland_ratio(Tc) * Tc))
@@ -132,7 +140,7 @@ def cavity(N=512, Ra=1e6, eps=0.6, Pr=0.71, gamma=1.4, tau0=None,
     picks tau0 (and, if the lattice is too coarse, a lower Ra) by tau_for."""
     Ra_req = Ra
     if tau0 is None:
-        tau0, Ra = tau_for(N, Ra, eps, Pr=Pr)
+        tau0, Ra = tau_for(N, Ra, eps, Pr=Pr, eos=int(eos[0]))
         bulk = bulk_ratio_for(Ra, stable=True)
     else:
         bulk = bulk_ratio_for(Ra, stable=False)

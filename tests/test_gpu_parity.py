@@ -147,6 +147,45 @@ def test_poiseuille_config2_fp32(orc, lbm):
     assert rel(mg["T"] - 1.0, mo["T"] - 1.0) < 1e-3
 
 
+@pytest.mark.parametrize("bx,by,pr", [(64, 5, 1), (128, 64, 1), (256, 16, 1), (128, 9, 2), (256, 32, 2),
+                                      (32, 7, 3), (128, 32, 3)])
+def test_paired_fp32_periodic_ragged(orc, lbm, bx, by, pr):
+    # odd width: the last pair of the last strip has one node only
+    cfg = W.periodic_box(201, 37, visc_law=2, eos=(W.EOS_CUBIC, (0.05, 0.2)), gamma=1.3,
+                         force=(2e-5, -1e-5), precision=1)
+    _, _, err = pair(orc, lbm, cfg, 100, seed=41, df=1e-4, tile=(bx, by, pr))
+    assert_close(err, TOL32)
+
+
+@pytest.mark.parametrize("tile", [(128, 16, 1), (64, 7, 1), (256, 16, 2)])
+def test_paired_fp32_walls(orc, lbm, tile):
+    cfg = W.cavity(N=67, Ra=1e3, eps=0.6, precision=1)
+    cfg["walls"][1]["u"] = (0.02, 0.0)
+    o, g, err = pair(orc, lbm, cfg, 1500, tile=tile)
+    assert_close(err, TOL32)
+    assert abs(g.nusselt(W.WALL_W) / o.nusselt(W.WALL_W) - 1) < 5e-3
+
+
+def test_paired_fp32_poiseuille_config2(orc, lbm):
+    cfg = W.poiseuille(nx=4, ny=128, precision=1)
+    o, g, err = pair(orc, lbm, cfg, 50000, tile=(64, 32, 2))
+    assert_close(err, TOL32)
+
+
+def test_paired_fp64_rejected(lbm):
+    g = lbm.Lattice(W.periodic_box(16, 8))
+    for pr in (1, 2, 3):
+        assert g.L.lbm_set_tile(g.h, 128, 8, pr) == lbm.LBM_EINVAL
+
+
+def test_lean_one_node_shape_matches_oracle(orc, lbm):
+    # pair 3 recomputes the macros at collision time; the compiler may contract
+    # that second copy differently, so it agrees with pair 0 to FP32 rounding
+    cfg = W.cavity(N=70, Ra=2e3, eps=0.5, precision=1)
+    _, _, err = pair(orc, lbm, cfg, 1500, tile=(64, 9, 3))
+    assert_close(err, TOL32)
+
+
 def test_couette_config1_fp32(orc, lbm):
     cfg = W.couette(nx=4, ny=64, precision=1)
     _, _, err = pair(orc, lbm, cfg, 20000)
@@ -221,8 +260,8 @@ def test_batch_equals_alone(lbm, graph_steps):
     mixed = [lbm.Lattice(c, stream=stream) for c in cfgs]
     alone[1].set_tile(64, 9)
     mixed[1].set_tile(64, 9)
-    alone[3].set_tile(32, 5)
-    mixed[3].set_tile(32, 5)
+    alone[3].set_tile(64, 5, 1)
+    mixed[3].set_tile(64, 5, 1)
     for a in alone[:2]:
         a.step(7)        # odd step count: the batch must respect each lattice's parity
     for m in mixed[:2]:
