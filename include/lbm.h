@@ -147,9 +147,11 @@ lbm_status lbm_derived(const lbm_ctx* ctx, double* out8);
  * macros in registers between the row pass and the collision, pair = 2
  * recomputes them (fewer registers, more threads per SM).  pair = 3 (FP32
  * storage only): one node per thread, bx = 32, 64 or 128, recomputing the
- * macros.  pair = 0 shapes of any width give identical results; pair 1-3
- * agree with them to FP32 rounding (their arithmetic is contracted
- * differently).
+ * macros.  pair = 4: one node per thread in warps that each own 30 columns
+ * and never synchronise with one another, bx = 30, 60 or 120 (1, 2 or 4
+ * warps per CTA), any precision.  pair = 0 and pair = 4 shapes of any width
+ * give identical results; pair 1-3 agree with them to FP32 rounding (their
+ * arithmetic is contracted differently).
  * Used by the autotuner. */
 lbm_status lbm_set_tile(lbm_ctx* ctx, int bx, int by, int pair);
 

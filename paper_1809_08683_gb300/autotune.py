@@ -53,12 +53,14 @@ def _store(d):
 
 
 PAIR_BX_CANDIDATES = (64, 128, 256)
+WARP_BX_CANDIDATES = (30, 60, 120)
 
 
 def candidates(cfg: dict):
     """(bx, by, pair) shapes worth timing for this lattice: one node per
-    thread for every precision, two nodes per thread for FP32 storage."""
-    shapes = [(bx, 0) for bx in BX_CANDIDATES]
+    thread in block strips or warp strips for every precision, two nodes per
+    thread for FP32 storage."""
+    shapes = [(bx, 0) for bx in BX_CANDIDATES] + [(bx, 4) for bx in WARP_BX_CANDIDATES]
     if int(cfg.get("precision", 0)) == 1:
         shapes += [(bx, 3) for bx in BX_CANDIDATES]
         shapes += [(bx, pr) for bx in PAIR_BX_CANDIDATES for pr in (1, 2)]
@@ -99,7 +101,7 @@ def tune(cfg: dict, steps: int = 20, force: bool = False, stream=None) -> tuple:
     with _lock:
         cache = _load()
         cache[key] = {"tile": list(best), "mlups": results[best],
-                      "all": {f"{b[0]}x{b[1]}{'p' if b[2] else ''}": v for b, v in results.items()}}
+                      "all": {f"{b[0]}x{b[1]}p{b[2]}": v for b, v in results.items()}}
         _store(cache)
     return best
 

@@ -22,6 +22,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -120,16 +121,17 @@ __device__ __forceinline__ uint32_t mix32(uint32_t h) {
 
 struct AddDither {
     mutable uint32_t h;
-    // f_i and g_i are independent variables, so one uniform draw serves both
+    // f_i and g_i are independent variables, so one uniform draw serves both.
+    // Draw: a Weyl step of the node's hash, its low 23 bits as the mantissa of
+    // a float in [1, 2), mapped to r * 2^-23 with r uniform in [-1/2, 1/2).
+    // Multiplying by 2^e (the stored value with its mantissa cleared) gives
+    // r * ulp for normal values and 0 for zero.
     __device__ __forceinline__ void operator()(float& f, float df, float& g, float dg) const {
-        h = h * 1664525u + 1013904223u;  // one LCG step per link
-        // 23 random mantissa bits: uniform in [1, 2), shifted to [-1/2, 1/2)
-        const float r = __int_as_float(0x3f800000u | (h >> 9)) - 1.5f;
-        // ulp of a normal float: 2^(exponent - 23); zero for zero
-        const float uf = __int_as_float(__float_as_int(f) & 0x7f800000) * 1.1920928955078125e-7f;
-        const float ug = __int_as_float(__float_as_int(g) & 0x7f800000) * 1.1920928955078125e-7f;
-        f = f + fmaf(r, uf, df);
-        g = g + fmaf(r, ug, dg);
+        h += 0x9e3779b9u;
+        const float r = fmaf(__int_as_float(0x3f800000u | (h & 0x007fffffu)), 1.1920928955078125e-7f,
+                             -1.7881393432617188e-7f);
+        f = f + fmaf(r, __int_as_float(__float_as_int(f) & 0x7f800000), df);
+        g = g + fmaf(r, __int_as_float(__float_as_int(g) & 0x7f800000), dg);
     }
     __device__ __forceinline__ void operator()(double& f, double df, double& g, double dg) const {
         f = f + df;
@@ -147,6 +149,49 @@ __device__ void rho_p_at(const Params<R>& P, const R* __restrict__ src, long lon
     node_macros(P, v, m);
     rd = m.rho_d;
     pd = m.p_d;
+}
+
+// Push streaming of one node's post-collision DFs v[0..17] (f then g) from
+// (x, j) into dst: population i moves to (x + e_ix, j + e_iy), wraps across
+// a periodic edge, or, leaving the lattice through a wall, lands reversed in
+// its own node's opposite slot (the bounce-back part of the wall treatment).
+template <typename R>
+__device__ __forceinline__ void push_node(R* __restrict__ dst, const R* v, int x, int j, int nx, int ny, int pitch,
+                                          long long plane, int px, int py) {
+    R* o = dst + ((long long)j * pitch + x);
+    if (x >= 1 && x <= nx - 2 && j >= 1 && j <= ny - 2) {
+        // interior: every population lands in the domain, no wrap;
+        // 18 planes fit 32-bit offsets (checked at creation)
+        const int pl = (int)plane;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int ex = (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+            const int ey = (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+            const int off = ey * pitch + ex;
+            o[i * pl + off] = v[i];
+            o[(9 + i) * pl + off] = v[9 + i];
+        }
+    } else {
+        // edge node: periodic wrap, or bounce-back into its own slot
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int ex = (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+            const int ey = (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+            const int opp = (i == 0) ? 0 : (i <= 4 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5);
+            int xd = x + ex, yd = j + ey;
+            bool out = false;
+            if (xd < 0 || xd >= nx) { if (px) xd = (xd < 0) ? nx - 1 : 0; else out = true; }
+            if (yd < 0 || yd >= ny) { if (py) yd = (yd < 0) ? ny - 1 : 0; else out = true; }
+            if (out) {
+                o[opp * plane] = v[i];
+                o[(9 + opp) * plane] = v[9 + i];
+            } else {
+                const long long t2 = (long long)yd * pitch + xd;
+                dst[i * plane + t2] = v[i];
+                dst[(9 + i) * plane + t2] = v[9 + i];
+            }
+        }
+    }
 }
 
 // ------------------------------------------------------------------------
@@ -300,8 +345,10 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
 
     // warp 0 issues the copies of logical row l into stage l % S; a row that
     // does not exist still completes its barrier phase (plain arrive)
+    int issued = 0, waited = 0;  // logical rows issued / waited for by this thread
     auto issue = [&](int l) {
         if (l > last_l || tid >= 32) return;
+        issued = l + 1;
         const int s = l % S;
         const int y = phys(l);
         if (tid == 0) {
@@ -328,6 +375,7 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
             s_abort = 1;
             return false;
         }
+        waited = l + 1;
         const R* st = stage + (size_t)s * 18 * W;
         const int slot = l & 3;
         if (active) {
@@ -338,9 +386,11 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
             s_rho[slot][c] = m.rho_d;
             s_p[slot][c] = m.p_d;
         }
-        // the two halo columns: lane 0 of warp 0 and the strip's last thread
-        // run the same instruction stream on their own chunk
-        const bool hl = (tid == 0 && has_l), hr = (tid == tlast && has_r);
+        // the two halo columns: two adjacent lanes of one warp run the same
+        // instruction stream on their own chunk, in warp 1 (not the warp
+        // that issues the copies) when the strip has more than one warp
+        constexpr int HL = BX >= 64 ? 32 : 0;
+        const bool hl = (tid == HL && has_l), hr = (tid == HL + 1 && has_r);
         if (hl || hr) {
             const int off = hl ? (xhl - xcl) : (E + BX + (xhr - xcr));
             const int col = hl ? 0 : tlast + 2;
@@ -351,15 +401,6 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
             node_macros(P, v, h);
             s_rho[slot][col] = h.rho_d;
             s_p[slot][col] = h.p_d;
-            if (hl && hr && tlast == 0) {
-                // a one-column strip owns both halos in the same thread
-                const int off2 = E + BX + (xhr - xcr);
-#pragma unroll
-                for (int q = 0; q < 18; ++q) v[q] = st[q * W + off2];
-                node_macros(P, v, h);
-                s_rho[slot][2] = h.rho_d;
-                s_p[slot][2] = h.p_d;
-            }
         }
         return true;
     };
@@ -433,47 +474,236 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
             AddDither add{mix32(step_hash ^ ((uint32_t)j * 0x85ebca77u + (uint32_t)x * 0xc2b2ae3du))};
             lbm::collide(P, mc, v, v + 9, grx, gry, gpx, gpy, add);
 
-            R* o = dst + ((long long)j * pitch + x);
-            if (x >= 1 && x <= nx - 2 && j >= 1 && j <= ny - 2) {
-                // interior: every population lands in the domain, no wrap;
-                // 18 planes fit 32-bit offsets (checked at creation)
-                const int pl = (int)plane;
-#pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    const int ex = (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
-                    const int ey = (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
-                    const int off = ey * pitch + ex;
-                    o[i * pl + off] = v[i];
-                    o[(9 + i) * pl + off] = v[9 + i];
-                }
-            } else {
-                // edge node: periodic wrap, or bounce-back into its own slot
-#pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    const int ex = (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
-                    const int ey = (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
-                    const int opp = (i == 0) ? 0 : (i <= 4 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5);
-                    int xd = x + ex, yd = j + ey;
-                    bool out = false;
-                    if (xd < 0 || xd >= nx) { if (px) xd = (xd < 0) ? nx - 1 : 0; else out = true; }
-                    if (yd < 0 || yd >= ny) { if (py) yd = (yd < 0) ? ny - 1 : 0; else out = true; }
-                    if (out) {
-                        o[opp * plane] = v[i];
-                        o[(9 + opp) * plane] = v[9 + i];
-                    } else {
-                        const long long t2 = (long long)yd * pitch + xd;
-                        dst[i * plane + t2] = v[i];
-                        dst[(9 + i) * plane + t2] = v[9 + i];
-                    }
-                }
-            }
+            push_node(dst, v, x, j, nx, ny, pitch, plane, px, py);
         }
         if (KEEP) mc = mn;
     }
     if (s_abort && tid == 0) {
-        // leave no bulk copy in flight into this CTA's shared memory
-        for (int l = 0; l <= last_l; ++l)
+        // leave no bulk copy in flight into this CTA's shared memory: wait,
+        // in order, for every row issued and not yet waited for
+        for (int l = waited; l < issued; ++l)
             if (phys(l) >= 0) mbar_wait(&bars[l % S], (uint32_t)((l / S) & 1));
+    }
+}
+
+// ------------------------------------------------------------------------
+// fused collide + stream, one autonomous warp per strip
+// ------------------------------------------------------------------------
+
+// Columns owned by one warp of k_collide_warp: lanes 1..30 own columns
+// wx0 .. wx0 + 29; lane 0 holds column wx0 - 1 and lane 31 column wx0 + 30,
+// whose macros the gradient stencil needs.
+constexpr int kWarpCols = 30;
+
+// Shared-memory layout of k_collide_warp: per warp, S stages of one lattice
+// row (18 planes, each [MW-element window][left wrap chunk][right wrap chunk])
+// and S mbarriers; then the parameters.  The window starts at the 16-byte
+// boundary at or below column wx0 - 1 and covers up to column wx0 + 30.
+template <typename R, int NW, int S>
+struct WarpSmem {
+    static constexpr int E = 16 / (int)sizeof(R);  // elements per 16-byte chunk
+    static constexpr int MW = 36;
+    static constexpr int W = MW + 2 * E;
+    static constexpr size_t stage_bytes = (size_t)18 * W * sizeof(R);
+    static constexpr size_t warp_bytes = (size_t)S * stage_bytes;
+    static constexpr size_t off_bars = (size_t)NW * warp_bytes;
+    static constexpr size_t off_params = (off_bars + 8 * NW * S + 15) / 16 * 16;
+    static constexpr size_t bytes = off_params + sizeof(Params<R>);
+};
+
+template <typename R>
+struct WarpTraits {
+    static constexpr int S = 3;
+    static constexpr int WARPS_PER_SM = sizeof(R) == 4 ? 16 : 8;  // caps registers at 128 (FP32) / 255 (FP64)
+};
+
+// Same per-node arithmetic as k_collide_stream, bit for bit, with no
+// block-wide synchronisation: each warp of the CTA sweeps its own strip of
+// kWarpCols columns over the CTA's rows, stages rows by TMA into its own
+// ring of stages, and takes the macros of the neighbouring columns from the
+// neighbouring lanes (warp shuffles) and those of the rows j - 1, j, j + 1
+// from its own registers.  Warps of a CTA only share the parameters.
+template <typename R, int NW, int S>
+__global__ void __launch_bounds__(32 * NW, WarpTraits<R>::WARPS_PER_SM / NW)
+    k_collide_warp(const Work* __restrict__ work, InstDesc* const* __restrict__ descs, int step_par,
+                   const long long* __restrict__ counter) {
+    using L = WarpSmem<R, NW, S>;
+    constexpr int E = L::E, MW = L::MW, W = L::W;
+    constexpr unsigned FULL = 0xffffffffu;
+    extern __shared__ __align__(128) unsigned char smem[];
+    Params<R>& P = *reinterpret_cast<Params<R>*>(smem + L::off_params);
+
+    const Work w = work[blockIdx.x];
+    const InstDesc* D = descs[w.inst];
+    load_params(&P, &dparams<R>(D));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    R* stage = reinterpret_cast<R*>(smem + (size_t)wid * L::warp_bytes);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::off_bars) + wid * S;
+    if (lane == 0) {
+        for (int k = 0; k < S; ++k) mbar_init(&bars[k], 1);
+        fence_mbar_init();
+    }
+    const int nx = D->nx, ny = D->ny, pitch = D->pitch, px = D->px, py = D->py;
+    const long long plane = D->plane;
+    const int b = w.par ^ step_par;
+    const R* __restrict__ src = reinterpret_cast<const R*>(D->buf[b]);
+    R* __restrict__ dst = reinterpret_cast<R*>(D->buf[b ^ 1]);
+    unsigned int* status = D->status;
+    const uint32_t step_hash = mix32((uint32_t)(w.step0 + *counter) * 0x9e3779b1u + 0x632be5abu);
+    __syncthreads();  // parameters and barrier initialisation visible; the last block-wide barrier
+
+    const int wx0 = w.x0 + kWarpCols * wid;
+    if (wx0 >= nx) return;  // whole warp beyond a ragged right edge
+    const int x = wx0 + lane - 1;  // this lane's column
+    const bool owned = lane >= 1 && lane <= kWarpCols && x < nx;
+    const int a = (max(wx0 - 1, 0) / E) * E;  // window start (16-byte aligned)
+    const int nmain = min(MW, pitch - a);     // pitch is a multiple of 32 elements
+    const bool wrap_l = px && wx0 == 0;                 // lane 0 holds column nx - 1
+    const bool wrap_r = px && wx0 + kWarpCols >= nx;    // lane nx - wx0 + 1 holds column 0
+    const int cl = ((nx - 1) / E) * E;
+    int off = -1;  // the lane's column in a stage row; -1: no column
+    if (x >= 0 && x < nx) off = x - a;
+    else if (x == -1 && wrap_l) off = MW + (nx - 1 - cl);
+    else if (x == nx && wrap_r) off = MW + E;
+    const uint32_t tx = (uint32_t)(18 * (nmain + (wrap_l ? E : 0) + (wrap_r ? E : 0)) * (int)sizeof(R));
+    const int nrows = w.y1 - w.y0;
+    const int last_l = nrows + 1;  // logical rows 0..last_l = physical y0-1..y1
+
+    auto phys = [&](int l) -> int {
+        int y = w.y0 - 1 + l;
+        if (y < 0 || y >= ny) {
+            if (!py) return -1;
+            y = (y < 0) ? y + ny : y - ny;
+        }
+        return y;
+    };
+
+    // the warp issues the copies of logical row l into its stage l % S; a row
+    // that does not exist still completes its barrier phase (plain arrive)
+    int issued = 0;  // logical rows whose copies this warp has issued
+    auto issue = [&](int l) {
+        if (l > last_l) return;
+        issued = l + 1;
+        const int s = l % S;
+        const int y = phys(l);
+        if (lane == 0) {
+            if (y < 0) mbar_arrive(&bars[s]);
+            else mbar_arrive_expect_tx(&bars[s], tx);
+        }
+        __syncwarp();
+        if (y >= 0 && lane < 18) {
+            fence_proxy_async();
+            const R* row = src + lane * plane + (long long)y * pitch;
+            R* st = stage + (size_t)s * 18 * W + (size_t)lane * W;
+            bulk_g2s(st, row + a, (uint32_t)(nmain * sizeof(R)), &bars[s]);
+            if (wrap_l) bulk_g2s(st + MW, row + cl, 16u, &bars[s]);
+            if (wrap_r) bulk_g2s(st + MW + E, row, 16u, &bars[s]);
+        }
+    };
+
+    // wait for logical row l; lanes holding a column return its macros
+    auto row_macros = [&](int l, Mac<R>& m, R& r, R& p) -> bool {
+        const int s = l % S;
+        const bool ok = __all_sync(FULL, mbar_wait(&bars[s], (uint32_t)((l / S) & 1)));
+        if (ok && off >= 0) {
+            const R* st = stage + (size_t)s * 18 * W + off;
+            R v[18];
+#pragma unroll
+            for (int q = 0; q < 18; ++q) v[q] = st[q * W];
+            node_macros(P, v, m);
+            r = m.rho_d;
+            p = m.p_d;
+        } else {
+            r = R(0);
+            p = R(0);
+        }
+        return ok;
+    };
+
+    for (int l = 0; l < S; ++l) issue(l);
+    int waited = 0;  // logical rows whose copies this warp has waited for
+    Mac<R> mc, mn;
+    R rm = R(0), pm = R(0), r0 = R(0), p0 = R(0), rp = R(0), pp = R(0);
+    bool ok = true;
+    if (phys(0) >= 0) ok = row_macros(0, mn, rm, pm);
+    if (ok) {
+        waited = 1;
+        ok = row_macros(1, mc, r0, p0);
+    }
+    if (ok) waited = 2;
+
+    for (int k = 0; ok && k < nrows; ++k) {
+        const int j = w.y0 + k;
+        if (phys(k + 2) >= 0) ok = row_macros(k + 2, mn, rp, pp);
+        if (!ok) break;
+        waited = k + 3;
+        issue(k + S);  // stage of logical row k is free: the warp's last collision read it
+
+        const R rml = __shfl_up_sync(FULL, rm, 1), rmr = __shfl_down_sync(FULL, rm, 1);
+        const R r0l = __shfl_up_sync(FULL, r0, 1), r0r = __shfl_down_sync(FULL, r0, 1);
+        const R rpl = __shfl_up_sync(FULL, rp, 1), rpr = __shfl_down_sync(FULL, rp, 1);
+        const R pml = __shfl_up_sync(FULL, pm, 1), pmr = __shfl_down_sync(FULL, pm, 1);
+        const R p0l = __shfl_up_sync(FULL, p0, 1), p0r = __shfl_down_sync(FULL, p0, 1);
+        const R ppl = __shfl_up_sync(FULL, pp, 1), ppr = __shfl_down_sync(FULL, pp, 1);
+        if (owned) {
+            if (!(isfinite(mc.rho_d) && isfinite(mc.T_d))) atomicOr(status, 1u);
+            const bool onS = !py && j == 0, onN = !py && j == ny - 1;
+            const bool onW = !px && x == 0, onE = !px && x == nx - 1;
+            R grx, gry, gpx, gpy;
+            if (!(onS || onN || onW || onE)) {
+                // grad = 3 sum_i w_i e_i phi(x + e_i), w = 1/9 (axis), 1/36 (diagonal)
+                const R t = R(1.0 / 3.0), d = R(1.0 / 12.0);
+                grx = t * (r0r - r0l) + d * ((rpr - rpl) + (rmr - rml));
+                gry = t * (rp - rm) + d * ((rpr - rmr) + (rpl - rml));
+                gpx = t * (p0r - p0l) + d * ((ppr - ppl) + (pmr - pml));
+                gpy = t * (pp - pm) + d * ((ppr - pmr) + (ppl - pml));
+            } else {
+                // wall node: one-sided second order along the inward normal,
+                // central along the wall
+                if (onW || onE) {
+                    const int dx = onW ? 1 : -1;
+                    R r2, p2;
+                    rho_p_at(P, src, plane, pitch, x + 2 * dx, j, r2, p2);
+                    const R r1 = onW ? r0r : r0l, p1 = onW ? p0r : p0l;
+                    grx = R(dx) * (R(-3) * r0 + R(4) * r1 - r2) * R(0.5);
+                    gpx = R(dx) * (R(-3) * p0 + R(4) * p1 - p2) * R(0.5);
+                } else {
+                    grx = (r0r - r0l) * R(0.5);
+                    gpx = (p0r - p0l) * R(0.5);
+                }
+                if (onS || onN) {
+                    const int dy = onS ? 1 : -1;
+                    R r2, p2;
+                    rho_p_at(P, src, plane, pitch, x, j + 2 * dy, r2, p2);
+                    const R r1 = onS ? rp : rm, p1 = onS ? pp : pm;
+                    gry = R(dy) * (R(-3) * r0 + R(4) * r1 - r2) * R(0.5);
+                    gpy = R(dy) * (R(-3) * p0 + R(4) * p1 - p2) * R(0.5);
+                } else {
+                    gry = (rp - rm) * R(0.5);
+                    gpy = (pp - pm) * R(0.5);
+                }
+            }
+
+            R v[18];
+            const R* st = stage + (size_t)((k + 1) % S) * 18 * W + off;
+#pragma unroll
+            for (int q = 0; q < 18; ++q) v[q] = st[q * W];
+            AddDither add{mix32(step_hash ^ ((uint32_t)j * 0x85ebca77u + (uint32_t)x * 0xc2b2ae3du))};
+            lbm::collide(P, mc, v, v + 9, grx, gry, gpx, gpy, add);
+            push_node(dst, v, x, j, nx, ny, pitch, plane, px, py);
+        }
+        mc = mn;
+        rm = r0; pm = p0;
+        r0 = rp; p0 = pp;
+    }
+    if (!ok) {
+        atomicOr(status, 2u);
+        // leave no bulk copy in flight into this warp's stages: wait, in
+        // order, for every row issued and not yet waited for
+        if (lane == 0)
+            for (int l = waited; l < issued; ++l)
+                if (phys(l) >= 0) mbar_wait(&bars[l % S], (uint32_t)((l / S) & 1));
+        __syncwarp();
     }
 }
 
@@ -516,25 +746,23 @@ __device__ void broadcast_params(const Params<float>& a, Params<f2>& b) {
 // Stochastic rounding of a pair of nodes: one draw per node and link.
 struct AddDither2 {
     mutable uint32_t h;
+    // the draw of AddDither, one per node of the pair and link
     __device__ __forceinline__ void operator()(f2& f, f2 df, f2& g, f2 dg) const {
-        h = h * 1664525u + 1013904223u;
-        const uint32_t h2 = h * 1664525u + 1013904223u;
-        h = h2;
-        const float2 r = make_float2(__int_as_float(0x3f800000u | (h >> 9)) - 1.5f,
-                                     __int_as_float(0x3f800000u | (h2 << 9 >> 9)) - 1.5f);
-        const float2 k = make_float2(1.1920928955078125e-7f, 1.1920928955078125e-7f);
-        const float2 uf = __fmul2_rn(make_float2(__int_as_float(__float_as_int(f.v.x) & 0x7f800000),
-                                                 __int_as_float(__float_as_int(f.v.y) & 0x7f800000)), k);
-        const float2 ug = __fmul2_rn(make_float2(__int_as_float(__float_as_int(g.v.x) & 0x7f800000),
-                                                 __int_as_float(__float_as_int(g.v.y) & 0x7f800000)), k);
-        f = f2(__fadd2_rn(f.v, __ffma2_rn(r, uf, df.v)));
-        g = f2(__fadd2_rn(g.v, __ffma2_rn(r, ug, dg.v)));
+        const uint32_t ha = h + 0x9e3779b9u, hb = ha + 0x9e3779b9u;
+        h = hb;
+        const float2 r = __ffma2_rn(make_float2(__int_as_float(0x3f800000u | (ha & 0x007fffffu)),
+                                                __int_as_float(0x3f800000u | (hb & 0x007fffffu))),
+                                    make_float2(1.1920928955078125e-7f, 1.1920928955078125e-7f),
+                                    make_float2(-1.7881393432617188e-7f, -1.7881393432617188e-7f));
+        const float2 ef = make_float2(__int_as_float(__float_as_int(f.v.x) & 0x7f800000),
+                                      __int_as_float(__float_as_int(f.v.y) & 0x7f800000));
+        const float2 eg = make_float2(__int_as_float(__float_as_int(g.v.x) & 0x7f800000),
+                                      __int_as_float(__float_as_int(g.v.y) & 0x7f800000));
+        f = f2(__fadd2_rn(f.v, __ffma2_rn(r, ef, df.v)));
+        g = f2(__fadd2_rn(g.v, __ffma2_rn(r, eg, dg.v)));
     }
 };
 
-// KEEP = true carries each thread's macros from the row pass to the
-// collision (more registers); KEEP = false recomputes them from the staged
-// DFs at collision time, which lets two nodes per thread fit 128 registers.
 template <int BX, bool KEEP>
 __global__ void __launch_bounds__(BX / 2, (KEEP ? 512 : 768) / BX) k_collide_pair(const Work* __restrict__ work,
                                                                     InstDesc* const* __restrict__ descs,
@@ -573,7 +801,6 @@ __global__ void __launch_bounds__(BX / 2, (KEEP ? 512 : 768) / BX) k_collide_pai
     const int xa = w.x0 + 2 * tid, xb = xa + 1;
     const bool act_a = xa < nx, act_b = xb < nx;
     const int xlast = min(w.x0 + BX, nx) - 1;
-    const int towner = (xlast - w.x0) >> 1;  // thread that owns the last column
     int xhl = w.x0 - 1;
     bool has_l = true;
     if (xhl < 0) { if (px) xhl = nx - 1; else has_l = false; }
@@ -596,8 +823,10 @@ __global__ void __launch_bounds__(BX / 2, (KEEP ? 512 : 768) / BX) k_collide_pai
         return y;
     };
 
+    int issued = 0, waited = 0;  // logical rows issued / waited for by this thread
     auto issue = [&](int l) {
         if (l > last_l || tid >= 32) return;
+        issued = l + 1;
         const int s = l % S;
         const int y = phys(l);
         if (tid == 0) {
@@ -622,6 +851,7 @@ __global__ void __launch_bounds__(BX / 2, (KEEP ? 512 : 768) / BX) k_collide_pai
             s_abort = 1;
             return false;
         }
+        waited = l + 1;
         const float* st = stage + (size_t)s * 18 * W;
         const int slot = l & 3;
         if (act_a) {
@@ -631,28 +861,30 @@ __global__ void __launch_bounds__(BX / 2, (KEEP ? 512 : 768) / BX) k_collide_pai
             f2 rd, jx, jy, sg;
             lbm::node_sums(v, v + 9, rd, jx, jy, sg);
             lbm::macros(P2, rd, jx, jy, sg, m);
-            *reinterpret_cast<float2*>(&s_rho[slot][ca]) = m.rho_d.v;
-            *reinterpret_cast<float2*>(&s_p[slot][ca]) = m.p_d.v;
+            if (act_b) {
+                *reinterpret_cast<float2*>(&s_rho[slot][ca]) = m.rho_d.v;
+                *reinterpret_cast<float2*>(&s_p[slot][ca]) = m.p_d.v;
+            } else {
+                // a half-filled last pair: its second column is the right
+                // halo, which another lane writes
+                s_rho[slot][ca] = m.rho_d.v.x;
+                s_p[slot][ca] = m.p_d.v.x;
+            }
         }
-        const bool hl = (tid == 0 && has_l), hr = (tid == towner && has_r);
+        // halo columns in scalar arithmetic, on two adjacent lanes of one
+        // warp (warp 1 when there are two or more), after their own pairs
+        constexpr int HL = BX / 2 >= 64 ? 32 : 0;
+        const bool hl = (tid == HL && has_l), hr = (tid == HL + 1 && has_r);
         if (hl || hr) {
-            // halo columns in scalar arithmetic, after this thread's own pair
+            const int off = hl ? (xhl - xcl) : (E + BX + (xhr - xcr));
+            const int col = hl ? 1 : cr;
             float v[18];
             Mac<float> h;
-            if (hl) {
 #pragma unroll
-                for (int q = 0; q < 18; ++q) v[q] = st[q * W + (xhl - xcl)];
-                node_macros(P1, v, h);
-                s_rho[slot][1] = h.rho_d;
-                s_p[slot][1] = h.p_d;
-            }
-            if (hr) {
-#pragma unroll
-                for (int q = 0; q < 18; ++q) v[q] = st[q * W + E + BX + (xhr - xcr)];
-                node_macros(P1, v, h);
-                s_rho[slot][cr] = h.rho_d;
-                s_p[slot][cr] = h.p_d;
-            }
+            for (int q = 0; q < 18; ++q) v[q] = st[q * W + off];
+            node_macros(P1, v, h);
+            s_rho[slot][col] = h.rho_d;
+            s_p[slot][col] = h.p_d;
         }
         return true;
     };
@@ -797,7 +1029,8 @@ __global__ void __launch_bounds__(BX / 2, (KEEP ? 512 : 768) / BX) k_collide_pai
         if (KEEP) mc = mn;
     }
     if (s_abort && tid == 0) {
-        for (int l = 0; l <= last_l; ++l)
+        // wait, in order, for every row issued and not yet waited for
+        for (int l = waited; l < issued; ++l)
             if (phys(l) >= 0) mbar_wait(&bars[l % S], (uint32_t)((l / S) & 1));
     }
 }
@@ -1312,6 +1545,7 @@ struct lbm_ctx {
     double* d_stage = nullptr;
     Work* d_work = nullptr;
     int n_work = 0, bx = 128, by = 0, pair = 0;
+    bool tile_set = false;  // launch shape chosen by lbm_set_tile, kept in batches
     BWork* d_bwork = nullptr;
     int n_bwork = 0;
     long steps = 0;
@@ -1323,6 +1557,15 @@ struct lbm_ctx {
     std::vector<BWork> h_bwork;
 };
 
+// Fused-kernel variants: strips of 32, 64, 128 columns, one node per thread
+// (indices 0-2, pair = 0); strips of 64, 128, 256 columns, two nodes per
+// thread in packed FP32 keeping the row macros in registers (indices 3-5,
+// pair = 1) or recomputing them at collision time (indices 6-8, pair = 2);
+// one node per thread recomputing the macros, fewer registers (indices 9-11,
+// pair = 3); one autonomous warp per 30 columns, 1, 2 or 4 warps per CTA
+// (indices 12-14, pair = 4).  Variants 3-11 need FP32 storage.
+constexpr int kVariants = 15;
+
 struct lbm_batch {
     std::vector<lbm_ctx*> ctxs;
     cudaStream_t stream = nullptr;
@@ -1330,7 +1573,7 @@ struct lbm_batch {
     Work* d_work = nullptr;
     BWork* d_bwork = nullptr;
     // launch groups: [precision][bx index] ranges of d_work; [precision] ranges of d_bwork
-    int w_off[2][12] = {{0}}, w_cnt[2][12] = {{0}};
+    int w_off[2][kVariants] = {{0}}, w_cnt[2][kVariants] = {{0}};
     int b_off[2] = {0, 0}, b_cnt[2] = {0, 0};
     long steps = 0;
     int graph_steps = 0;
@@ -1340,15 +1583,18 @@ struct lbm_batch {
 
 namespace {
 
+// Work items of one lattice: strips of bx columns, each cut into
+// ceil(ny / by) runs of rows whose lengths differ by at most one.
 std::vector<Work> make_work(const lbm_config& c, int inst, int bx, int by, int par, long long step0) {
     std::vector<Work> v;
-    for (int y0 = 0; y0 < c.ny; y0 += by)
+    const long long nruns = (c.ny + by - 1) / by;
+    for (long long r = 0; r < nruns; ++r)
         for (int x0 = 0; x0 < c.nx; x0 += bx) {
             Work w{};
             w.inst = inst;
             w.x0 = x0;
-            w.y0 = y0;
-            w.y1 = std::min(y0 + by, c.ny);
+            w.y0 = (int)(r * c.ny / nruns);
+            w.y1 = (int)((r + 1) * c.ny / nruns);
             w.par = par;
             w.step0 = step0;
             v.push_back(w);
@@ -1382,11 +1628,27 @@ void ensure_tick(std::vector<BWork>& v, int inst, int par) {
     }
 }
 
-int default_rows(const lbm_config& c, int bx) {
-    // enough CTAs to cover 152 SMs several times, runs of at most 64 rows
+// Default launch shape.  FP32 storage: warp strips (pair 4), one warp per
+// CTA; FP64 storage, whose node update is bound by the FP64 pipe rather than
+// by synchronisation: block strips of 128 columns (pair 0).  Both give the
+// same bits as any other pair-0/pair-4 shape.
+void default_shape(const lbm_config& c, int& bx, int& pair) {
+    if (c.precision == LBM_FP32_DEV) { bx = 30; pair = 4; }
+    else { bx = 128; pair = 0; }
+}
+
+// Rows per run inside a batch, whose CTAs fill the GPU many times over:
+// runs of about 32 (FP32) or 16 (FP64) rows measured best on 4096^2 and
+// 2048^2 lattices (longer runs lose DRAM and L2 locality between CTAs
+// resident at the same time, shorter ones re-stage more halo rows).
+int batch_rows(const lbm_config& c) { return std::min(c.ny, c.precision == LBM_FP32_DEV ? 32 : 16); }
+
+// Rows per run for a lattice launched on its own: the batch length, halved
+// (down to 8) while the lattice gives fewer CTAs than the GPU holds.
+int default_rows(const lbm_config& c, int bx, int resident) {
     const long long strips = (c.nx + bx - 1) / bx;
-    long long by = 32;
-    while (by > 4 && strips * ((c.ny + by - 1) / by) < 4 * 152) by /= 2;
+    long long by = batch_rows(c);
+    while (by > 8 && strips * ((c.ny + by - 1) / by) < resident) by /= 2;
     return (int)std::max<long long>(1, std::min<long long>(by, c.ny));
 }
 
@@ -1408,6 +1670,16 @@ cudaError_t configure_collide() {
     if (e != cudaSuccess) return e;
     // prefer shared memory over L1: the row stages, not L1, feed the kernel
     return cudaFuncSetAttribute(k_collide_stream<R, BX, S, KEEP>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared);
+}
+
+template <typename R, int NW>
+cudaError_t configure_warp() {
+    constexpr int S = WarpTraits<R>::S;
+    cudaError_t e = cudaFuncSetAttribute(k_collide_warp<R, NW, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)WarpSmem<R, NW, S>::bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_collide_warp<R, NW, S>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                 (int)cudaSharedmemCarveoutMaxShared);
 }
 
@@ -1440,6 +1712,12 @@ lbm_status configure_kernels() {
     if (e == cudaSuccess) e = configure_collide<double, 32>();
     if (e == cudaSuccess) e = configure_collide<double, 64>();
     if (e == cudaSuccess) e = configure_collide<double, 128>();
+    if (e == cudaSuccess) e = configure_warp<float, 1>();
+    if (e == cudaSuccess) e = configure_warp<float, 2>();
+    if (e == cudaSuccess) e = configure_warp<float, 4>();
+    if (e == cudaSuccess) e = configure_warp<double, 1>();
+    if (e == cudaSuccess) e = configure_warp<double, 2>();
+    if (e == cudaSuccess) e = configure_warp<double, 4>();
     if (e != cudaSuccess) return fail(LBM_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
     done = 1;
     return LBM_OK;
@@ -1452,21 +1730,21 @@ void launch_collide_bx(const Work* work, int n, InstDesc* const* descs, int par,
     k_collide_stream<R, BX, S, KEEP><<<n, BX, FusedSmem<R, BX, S>::bytes, s>>>(work, descs, par, counter);
 }
 
+template <typename R, int NW>
+void launch_warp_nw(const Work* work, int n, InstDesc* const* descs, int par, const long long* counter,
+                    cudaStream_t s) {
+    constexpr int S = WarpTraits<R>::S;
+    k_collide_warp<R, NW, S><<<n, 32 * NW, WarpSmem<R, NW, S>::bytes, s>>>(work, descs, par, counter);
+}
+
 template <int BX, bool KEEP>
 void launch_pair_bx(const Work* work, int n, InstDesc* const* descs, int par, const long long* counter,
                     cudaStream_t s) {
     k_collide_pair<BX, KEEP><<<n, BX / 2, PairSmem<BX>::bytes, s>>>(work, descs, par, counter);
 }
 
-// Fused-kernel variants: strips of 32, 64, 128 columns, one node per thread
-// (indices 0-2, pair = 0); strips of 64, 128, 256 columns, two nodes per
-// thread in packed FP32 keeping the row macros in registers (indices 3-5,
-// pair = 1) or recomputing them at collision time (indices 6-8, pair = 2);
-// one node per thread recomputing the macros, fewer registers (indices 9-11,
-// pair = 3).  Variants 3-11 need FP32 storage.
-constexpr int kVariants = 12;
-static const int kVariantWidth[kVariants] = {32, 64, 128, 64, 128, 256, 64, 128, 256, 32, 64, 128};
-static const int kVariantPair[kVariants] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3};
+static const int kVariantWidth[kVariants] = {32, 64, 128, 64, 128, 256, 64, 128, 256, 32, 64, 128, 30, 60, 120};
+static const int kVariantPair[kVariants] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 4, 4, 4};
 
 int variant_index(int bx, int pair) {
     for (int v = 0; v < kVariants; ++v)
@@ -1490,6 +1768,9 @@ void launch_collide(const Work* work, int n, int variant, InstDesc* const* descs
     case 9: launch_collide_bx<R, 32, false>(work, n, descs, par, counter, s); break;
     case 10: launch_collide_bx<R, 64, false>(work, n, descs, par, counter, s); break;
     case 11: launch_collide_bx<R, 128, false>(work, n, descs, par, counter, s); break;
+    case 12: launch_warp_nw<R, 1>(work, n, descs, par, counter, s); break;
+    case 13: launch_warp_nw<R, 2>(work, n, descs, par, counter, s); break;
+    case 14: launch_warp_nw<R, 4>(work, n, descs, par, counter, s); break;
     default: launch_collide_bx<R, 128>(work, n, descs, par, counter, s); break;
     }
 }
@@ -1607,8 +1888,18 @@ lbm_status lbm_create(const lbm_config* cfg, void* workspace, size_t workspace_b
     InstDesc* p = c->d_desc;
     if (cudaMemcpyAsync(c->d_descs, &p, sizeof(p), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
         return cleanup(fail(LBM_ECUDA, "descs upload"));
-    c->bx = 128;
-    c->by = default_rows(*cfg, c->bx);
+    default_shape(*cfg, c->bx, c->pair);
+    {
+        int dev = 0, sms = 152, per_sm = 4;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cfg->precision == LBM_FP32_DEV)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_collide_warp<float, 1, WarpTraits<float>::S>, 32,
+                                                          WarpSmem<float, 1, WarpTraits<float>::S>::bytes);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_collide_stream<double, 128, FusedTraits<double, 128>::S, true>,
+                                                          128, FusedSmem<double, 128, FusedTraits<double, 128>::S>::bytes);
+        c->by = default_rows(*cfg, c->bx, sms * std::max(per_sm, 1));
+    }
     if ((st = upload_work(c)) != LBM_OK) return cleanup(st);
     c->h_bwork = make_bwork(*cfg, 0, 0);
     ensure_tick(c->h_bwork, 0, 0);
@@ -1762,14 +2053,17 @@ lbm_status lbm_derived(const lbm_ctx* c, double* out8) {
 
 lbm_status lbm_set_tile(lbm_ctx* c, int bx, int by, int pair) {
     if (!c) return fail(LBM_EINVAL, "null ctx");
-    if (pair && c->cfg.precision != LBM_FP32_DEV) return fail(LBM_EINVAL, "paired packed-FP32 strips need FP32 storage");
+    if (pair >= 1 && pair <= 3 && c->cfg.precision != LBM_FP32_DEV)
+        return fail(LBM_EINVAL, "pair 1-3 need FP32 storage");
     if (variant_index(bx, pair) < 0)
-        return fail(LBM_EINVAL, pair ? "paired strips (pair 1 or 2) are 64, 128 or 256 columns"
-                                     : "bx must be 32, 64 or 128");
+        return fail(LBM_EINVAL, pair == 4                ? "warp strips (pair 4) are 30, 60 or 120 columns"
+                                : (pair == 1 || pair == 2) ? "paired strips (pair 1 or 2) are 64, 128 or 256 columns"
+                                                           : "bx must be 32, 64 or 128");
     if (by < 1) return fail(LBM_EINVAL, "by must be >= 1");
     c->bx = bx;
     c->pair = pair;
     c->by = std::min(by, c->cfg.ny);
+    c->tile_set = true;
     lbm_status st = upload_work(c);
     if (st != LBM_OK) return st;
     CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -1791,7 +2085,7 @@ lbm_status lbm_step(lbm_ctx* c, long nsteps) {
             launch_collide<float>(c->d_work, c->n_work, variant_index(c->bx, c->pair), c->d_descs, par, c->d_counter, c->stream);
             launch_boundary<float>(c->d_bwork, c->n_bwork, c->d_descs, par, c->d_counter, c->stream);
         } else {
-            launch_collide<double>(c->d_work, c->n_work, variant_index(c->bx, 0), c->d_descs, par, c->d_counter, c->stream);
+            launch_collide<double>(c->d_work, c->n_work, variant_index(c->bx, c->pair), c->d_descs, par, c->d_counter, c->stream);
             launch_boundary<double>(c->d_bwork, c->n_bwork, c->d_descs, par, c->d_counter, c->stream);
         }
     }
@@ -2046,12 +2340,17 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, int graph_steps, lbm_ba
         descs.push_back(c->d_desc);
         const int pr = is_fp32(c) ? 1 : 0, bi = variant_index(c->bx, c->pair);
         const int par = (int)(c->steps & 1);
-        auto w = make_work(c->cfg, i, c->bx, c->by, par, c->steps);
+        auto w = make_work(c->cfg, i, c->bx, c->tile_set ? c->by : batch_rows(c->cfg), par, c->steps);
         groups[pr][bi].insert(groups[pr][bi].end(), w.begin(), w.end());
         auto bw = make_bwork(c->cfg, i, par);
         bgroups[pr].insert(bgroups[pr].end(), bw.begin(), bw.end());
     }
     std::vector<Work> all;
+    // longest runs first within each launch, so that short ones fill the tail
+    for (int pr = 0; pr < 2; ++pr)
+        for (int bi = 0; bi < kVariants; ++bi)
+            std::stable_sort(groups[pr][bi].begin(), groups[pr][bi].end(),
+                             [](const Work& a, const Work& b) { return a.y1 - a.y0 > b.y1 - b.y0; });
     for (int pr = 0; pr < 2; ++pr)
         for (int bi = 0; bi < kVariants; ++bi) {
             b->w_off[pr][bi] = (int)all.size();

@@ -27,9 +27,27 @@
 
 namespace lbm {
 
-// Division and reciprocal: exact in FP64; in FP32 the fast hardware
-// division (a few ulp), which the FP32 path's 1e-4 tolerance absorbs.
-LBM_HD double fdiv(double a, double b) { return a / b; }
+// Division in the per-node arithmetic.  FP32: the fast hardware division
+// (a few ulp), which the FP32 path's 1e-4 tolerance absorbs.  FP64 on the
+// device: a * (1/b), with 1/b from the hardware's approximate FP64
+// reciprocal (PTX rcp.approx.ftz.f64, about 20 correct bits) refined by two
+// Newton-Raphson steps y <- y + y (1 - b y), each of which doubles the
+// correct bits (20 -> 40 -> beyond 53): within 2 ulp of the quotient.  The
+// divisors are O(1) lattice quantities (densities, temperatures, 1 + eta/rho
+// terms), never subnormal.
+LBM_HD double fdiv(double a, double b) {
+#if defined(__CUDA_ARCH__)
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(b));
+    double e = fma(-b, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-b, y, 1.0);
+    y = fma(y, e, y);
+    return a * y;
+#else
+    return a / b;
+#endif
+}
 LBM_HD float fdiv(float a, float b) {
 #if defined(__CUDA_ARCH__)
     return __fdividef(a, b);

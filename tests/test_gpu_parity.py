@@ -178,6 +178,48 @@ def test_paired_fp64_rejected(lbm):
         assert g.L.lbm_set_tile(g.h, 128, 8, pr) == lbm.LBM_EINVAL
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("bx,by", [(30, 1), (60, 5), (120, 37), (120, 4)])
+def test_warp_strips_periodic_ragged(orc, lbm, precision, bx, by):
+    # 200 columns: the last warp strip is 20 columns wide, the last CTA ragged
+    cfg = W.periodic_box(200, 37, visc_law=2, eos=(W.EOS_CUBIC, (0.05, 0.2)), gamma=1.3,
+                         force=(2e-5, -1e-5), precision=precision)
+    _, _, err = pair(orc, lbm, cfg, 60, seed=43, df=1e-4, tile=(bx, by, 4))
+    assert_close(err, TOL32 if precision else TOL64)
+
+
+@pytest.mark.parametrize("nx,ny", [(3, 3), (1, 8), (31, 5), (32, 4)])
+def test_warp_strips_small_periodic_fp64(orc, lbm, nx, ny):
+    # both wrap chunks in one warp; a strip narrower than the warp
+    cfg = W.periodic_box(nx, ny, visc_law=2, eos=(W.EOS_IDEAL, ()), force=(1e-5, -2e-5))
+    _, _, err = pair(orc, lbm, cfg, 300, seed=nx * 100 + ny, df=1e-4, tile=(120, 2, 4))
+    assert_close(err, TOL64)
+
+
+@pytest.mark.parametrize("tile", [(120, 16, 4), (30, 7, 4)])
+def test_warp_strips_walls_fp64(orc, lbm, tile):
+    cfg = W.cavity(N=67, Ra=1e3, eps=0.6, tau0=0.8)
+    cfg["walls"][1]["u"] = (0.02, 0.0)
+    o, g, err = pair(orc, lbm, cfg, 1000, tile=tile)
+    assert_close(err, TOL64)
+    assert abs(g.nusselt(W.WALL_W) / o.nusselt(W.WALL_W) - 1) < 1e-10
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_warp_strips_equal_block_strips(lbm, precision):
+    # the warp-strip kernel runs the per-node arithmetic of the block-strip
+    # kernel on the same inputs: the two give the same bits
+    cfg = W.cavity(N=97, Ra=2e3, eps=0.5, precision=precision)
+    a, b = lbm.Lattice(cfg), lbm.Lattice(cfg)
+    a.set_tile(128, 16, 0)
+    b.set_tile(60, 11, 4)
+    a.step(300)
+    b.step(300)
+    fa, ga = a.get_state()
+    fb, gb = b.get_state()
+    assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+
+
 def test_lean_one_node_shape_matches_oracle(orc, lbm):
     # pair 3 recomputes the macros at collision time; the compiler may contract
     # that second copy differently, so it agrees with pair 0 to FP32 rounding
