@@ -149,11 +149,20 @@ lbm_status lbm_derived(const lbm_ctx* ctx, double* out8);
  * storage only): one node per thread, bx = 32, 64 or 128, recomputing the
  * macros.  pair = 4: one node per thread in warps that each own 30 columns
  * and never synchronise with one another, bx = 30, 60 or 120 (1, 2 or 4
- * warps per CTA), any precision.  pair = 0 and pair = 4 shapes of any width
- * give identical results; pair 1-3 agree with them to FP32 rounding (their
+ * warps per CTA), any precision.  pair = 5 (FP32 storage only): warp
+ * strips of 60 columns, two neighbouring nodes per lane in packed FP32,
+ * bx = 60, 120 or 240.  pair = 0 and pair = 4 shapes of any width give
+ * identical results; pairs 1-3 and 5 agree with them to FP32 rounding (their
  * arithmetic is contracted differently).
  * Used by the autotuner. */
 lbm_status lbm_set_tile(lbm_ctx* ctx, int bx, int by, int pair);
+
+/* Launch shape in use: the default chosen by lbm_create (FP32 storage: warp
+ * strips, pair = 4, bx = 30; FP64: pair = 0, bx = 128; by from the lattice
+ * size and the GPU's occupancy) or the one set by lbm_set_tile.  by is the
+ * run length when the lattice is stepped alone; a batch shortens the runs
+ * of members whose shape was not set until it fills the GPU. */
+lbm_status lbm_get_tile(const lbm_ctx* ctx, int* bx, int* by, int* pair);
 
 /* Steps taken since the last (re)initialisation. */
 long lbm_step_count(const lbm_ctx* ctx);

@@ -54,6 +54,7 @@ def _store(d):
 
 PAIR_BX_CANDIDATES = (64, 128, 256)
 WARP_BX_CANDIDATES = (30, 60, 120)
+WARP2_BX_CANDIDATES = (60, 120, 240)
 
 
 def candidates(cfg: dict):
@@ -64,6 +65,7 @@ def candidates(cfg: dict):
     if int(cfg.get("precision", 0)) == 1:
         shapes += [(bx, 3) for bx in BX_CANDIDATES]
         shapes += [(bx, pr) for bx in PAIR_BX_CANDIDATES for pr in (1, 2)]
+        shapes += [(bx, 5) for bx in WARP2_BX_CANDIDATES]
     out = []
     for bx, pr in shapes:
         if bx > 32 and cfg["nx"] <= bx // 2:

@@ -194,6 +194,63 @@ __device__ __forceinline__ void push_node(R* __restrict__ dst, const R* v, int x
     }
 }
 
+// Push streaming of a pair of nodes (xa, j), (xa + 1, j) in packed FP32:
+// populations that stream along y only land as one 8-byte store (xa is even
+// and the pitch a multiple of 32); an edge pair goes node by node with
+// periodic wrap or bounce-back.  act_b = false: only node xa exists.
+__device__ __forceinline__ void push_pair(float* __restrict__ dst, const f2* v, int xa, bool act_b, int j, int nx, int ny,
+                                          int pitch, long long plane, int px, int py) {
+    const int xb = xa + 1;
+    if (act_b && xa >= 1 && xb <= nx - 2 && j >= 1 && j <= ny - 2) {
+        // both nodes interior: no wrap, no bounce-back
+        float* o = dst + ((long long)j * pitch + xa);
+        const int pl = (int)plane;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int ex = (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+            const int ey = (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+            const int off = ey * pitch + ex;
+            if (ex == 0) {
+                *reinterpret_cast<float2*>(o + i * pl + off) = v[i].v;
+                *reinterpret_cast<float2*>(o + (9 + i) * pl + off) = v[9 + i].v;
+            } else {
+                o[i * pl + off] = v[i].v.x;
+                o[i * pl + off + 1] = v[i].v.y;
+                o[(9 + i) * pl + off] = v[9 + i].v.x;
+                o[(9 + i) * pl + off + 1] = v[9 + i].v.y;
+            }
+        }
+    } else {
+        // edge pair: per node, periodic wrap or bounce-back into its own slot
+#pragma unroll
+        for (int lane = 0; lane < 2; ++lane) {
+            if (lane && !act_b) break;
+            const int x = lane ? xb : xa;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const int ex = (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+                const int ey = (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+                const int opp = (i == 0) ? 0 : (i <= 4 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5);
+                const float fv = lane ? v[i].v.y : v[i].v.x;
+                const float gv = lane ? v[9 + i].v.y : v[9 + i].v.x;
+                int xd = x + ex, yd = j + ey;
+                bool out = false;
+                if (xd < 0 || xd >= nx) { if (px) xd = (xd < 0) ? nx - 1 : 0; else out = true; }
+                if (yd < 0 || yd >= ny) { if (py) yd = (yd < 0) ? ny - 1 : 0; else out = true; }
+                if (out) {
+                    const long long t2 = (long long)j * pitch + x;
+                    dst[opp * plane + t2] = fv;
+                    dst[(9 + opp) * plane + t2] = gv;
+                } else {
+                    const long long t2 = (long long)yd * pitch + xd;
+                    dst[i * plane + t2] = fv;
+                    dst[(9 + i) * plane + t2] = gv;
+                }
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------------
 // TMA bulk copies and mbarriers (inline PTX, sm_90+ forms valid on sm_103a)
 // ------------------------------------------------------------------------
@@ -977,54 +1034,7 @@ __global__ void __launch_bounds__(BX / 2, (KEEP ? 512 : 768) / BX) k_collide_pai
             AddDither2 add{mix32(step_hash ^ ((uint32_t)j * 0x85ebca77u + (uint32_t)xa * 0xc2b2ae3du))};
             lbm::collide(P2, mc, v, v + 9, grx, gry, gpx, gpy, add);
 
-            if (act_b && xa >= 1 && xb <= nx - 2 && j >= 1 && j <= ny - 2) {
-                // both nodes interior: no wrap, no bounce-back
-                float* o = dst + ((long long)j * pitch + xa);
-                const int pl = (int)plane;
-#pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    const int ex = (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
-                    const int ey = (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
-                    const int off = ey * pitch + ex;
-                    if (ex == 0) {
-                        *reinterpret_cast<float2*>(o + i * pl + off) = v[i].v;
-                        *reinterpret_cast<float2*>(o + (9 + i) * pl + off) = v[9 + i].v;
-                    } else {
-                        o[i * pl + off] = v[i].v.x;
-                        o[i * pl + off + 1] = v[i].v.y;
-                        o[(9 + i) * pl + off] = v[9 + i].v.x;
-                        o[(9 + i) * pl + off + 1] = v[9 + i].v.y;
-                    }
-                }
-            } else {
-                // edge pair: per node, periodic wrap or bounce-back into its own slot
-#pragma unroll
-                for (int lane = 0; lane < 2; ++lane) {
-                    if (lane && !act_b) break;
-                    const int x = lane ? xb : xa;
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) {
-                        const int ex = (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
-                        const int ey = (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
-                        const int opp = (i == 0) ? 0 : (i <= 4 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5);
-                        const float fv = lane ? v[i].v.y : v[i].v.x;
-                        const float gv = lane ? v[9 + i].v.y : v[9 + i].v.x;
-                        int xd = x + ex, yd = j + ey;
-                        bool out = false;
-                        if (xd < 0 || xd >= nx) { if (px) xd = (xd < 0) ? nx - 1 : 0; else out = true; }
-                        if (yd < 0 || yd >= ny) { if (py) yd = (yd < 0) ? ny - 1 : 0; else out = true; }
-                        if (out) {
-                            const long long t2 = (long long)j * pitch + x;
-                            dst[opp * plane + t2] = fv;
-                            dst[(9 + opp) * plane + t2] = gv;
-                        } else {
-                            const long long t2 = (long long)yd * pitch + xd;
-                            dst[i * plane + t2] = fv;
-                            dst[(9 + i) * plane + t2] = gv;
-                        }
-                    }
-                }
-            }
+            push_pair(dst, v, xa, act_b, j, nx, ny, pitch, plane, px, py);
         }
         if (KEEP) mc = mn;
     }
@@ -1032,6 +1042,265 @@ __global__ void __launch_bounds__(BX / 2, (KEEP ? 512 : 768) / BX) k_collide_pai
         // wait, in order, for every row issued and not yet waited for
         for (int l = waited; l < issued; ++l)
             if (phys(l) >= 0) mbar_wait(&bars[l % S], (uint32_t)((l / S) & 1));
+    }
+}
+
+// ------------------------------------------------------------------------
+// fused collide + stream, one autonomous warp per strip, two nodes per lane
+// ------------------------------------------------------------------------
+
+// Columns owned by one warp of k_collide_warp2: lane L = 1..30 owns the
+// columns wx0 + 2L - 2 and wx0 + 2L - 1; lane 0 holds column wx0 - 1 (its
+// second element) and lane 31 column wx0 + 60 (its first element).
+constexpr int kWarp2Cols = 60;
+
+template <int NW, int S>
+struct Warp2Smem {
+    static constexpr int E = 4;   // floats per 16-byte chunk
+    static constexpr int MW = 68; // window: columns floor4(wx0 - 2) .. wx0 + 60 and beyond
+    static constexpr int W = MW + 2 * E;
+    static constexpr size_t stage_bytes = (size_t)18 * W * sizeof(float);
+    static constexpr size_t warp_bytes = (size_t)S * stage_bytes;
+    static constexpr size_t off_bars = (size_t)NW * warp_bytes;
+    static constexpr size_t off_p2 = (off_bars + 8 * NW * S + 15) / 16 * 16;
+    static constexpr size_t off_p1 = (off_p2 + sizeof(Params<f2>) + 15) / 16 * 16;
+    static constexpr size_t bytes = off_p1 + sizeof(Params<float>);
+};
+
+// The warp-strip scheme of k_collide_warp with the node arithmetic of
+// k_collide_pair: each lane evaluates two neighbouring nodes at once in
+// packed FP32 (lbm_f2.cuh), including the macros of the strip's halo
+// columns.  Neighbour macros come from the lane itself (the other node of
+// its pair) or from the adjacent lane by shuffle.
+#ifndef LBM_WARP2_WARPS_PER_SM
+#define LBM_WARP2_WARPS_PER_SM 8  // resident warps per SM the register budget allows
+#endif
+
+template <int NW, int S>
+__global__ void __launch_bounds__(32 * NW, LBM_WARP2_WARPS_PER_SM / NW)
+    k_collide_warp2(const Work* __restrict__ work, InstDesc* const* __restrict__ descs, int step_par,
+                    const long long* __restrict__ counter) {
+    using L = Warp2Smem<NW, S>;
+    constexpr int E = L::E, MW = L::MW, W = L::W;
+    constexpr unsigned FULL = 0xffffffffu;
+    extern __shared__ __align__(128) unsigned char smem[];
+    Params<f2>& P2 = *reinterpret_cast<Params<f2>*>(smem + L::off_p2);
+    Params<float>& P1 = *reinterpret_cast<Params<float>*>(smem + L::off_p1);
+
+    const Work w = work[blockIdx.x];
+    const InstDesc* D = descs[w.inst];
+    load_params(&P1, &D->pf);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float* stage = reinterpret_cast<float*>(smem + (size_t)wid * L::warp_bytes);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::off_bars) + wid * S;
+    if (lane == 0) {
+        for (int k = 0; k < S; ++k) mbar_init(&bars[k], 1);
+        fence_mbar_init();
+    }
+    const int nx = D->nx, ny = D->ny, pitch = D->pitch, px = D->px, py = D->py;
+    const long long plane = D->plane;
+    const int b = w.par ^ step_par;
+    const float* __restrict__ src = reinterpret_cast<const float*>(D->buf[b]);
+    float* __restrict__ dst = reinterpret_cast<float*>(D->buf[b ^ 1]);
+    unsigned int* status = D->status;
+    const uint32_t step_hash = mix32((uint32_t)(w.step0 + *counter) * 0x9e3779b1u + 0x632be5abu);
+    __syncthreads();
+    if (threadIdx.x == 0) broadcast_params(P1, P2);
+    __syncthreads();  // the last block-wide barrier
+
+    const int wx0 = w.x0 + kWarp2Cols * wid;
+    if (wx0 >= nx) return;
+    const int xa = wx0 + 2 * lane - 2, xb = xa + 1;
+    const bool own = lane >= 1 && lane <= kWarp2Cols / 2;
+    const bool act_a = own && xa < nx, act_b = own && xb < nx;
+    const int a0 = (max(wx0 - 2, 0) / E) * E;
+    const int nmain = min(MW, pitch - a0);
+    const bool wrap_l = px && wx0 == 0;
+    const bool wrap_r = px && wx0 + kWarp2Cols >= nx;
+    const int cl = ((nx - 1) / E) * E;
+    // stage offset of column x as seen from this warp, or -1 if not held
+    auto offset_of = [&](int x) -> int {
+        if (x >= 0 && x < nx && x >= a0 && x - a0 < nmain) return x - a0;
+        if (x == -1 && wrap_l) return MW + (nx - 1 - cl);
+        if (x == nx && wrap_r) return MW + E;
+        return -1;
+    };
+    const int offa = offset_of(xa), offb = offset_of(xb);
+    const bool fast = offa >= 0 && offb == offa + 1;  // offa is even: one 8-byte load per plane
+    const uint32_t tx = (uint32_t)(18 * (nmain + (wrap_l ? E : 0) + (wrap_r ? E : 0)) * (int)sizeof(float));
+    const int nrows = w.y1 - w.y0;
+    const int last_l = nrows + 1;
+
+    auto phys = [&](int l) -> int {
+        int y = w.y0 - 1 + l;
+        if (y < 0 || y >= ny) {
+            if (!py) return -1;
+            y = (y < 0) ? y + ny : y - ny;
+        }
+        return y;
+    };
+
+    int issued = 0;
+    auto issue = [&](int l) {
+        if (l > last_l) return;
+        issued = l + 1;
+        const int s = l % S;
+        const int y = phys(l);
+        if (lane == 0) {
+            if (y < 0) mbar_arrive(&bars[s]);
+            else mbar_arrive_expect_tx(&bars[s], tx);
+        }
+        __syncwarp();
+        if (y >= 0 && lane < 18) {
+            fence_proxy_async();
+            const float* row = src + lane * plane + (long long)y * pitch;
+            float* st = stage + (size_t)s * 18 * W + (size_t)lane * W;
+            bulk_g2s(st, row + a0, (uint32_t)(nmain * sizeof(float)), &bars[s]);
+            if (wrap_l) bulk_g2s(st + MW, row + cl, 16u, &bars[s]);
+            if (wrap_r) bulk_g2s(st + MW + E, row, 16u, &bars[s]);
+        }
+    };
+
+    // the lane's two nodes from stage s (a column not held reads as 0)
+    auto load_pair = [&](int s, f2* v) {
+        const float* st = stage + (size_t)s * 18 * W;
+        if (fast) {
+#pragma unroll
+            for (int q = 0; q < 18; ++q) v[q] = f2(*reinterpret_cast<const float2*>(st + q * W + offa));
+        } else {
+#pragma unroll
+            for (int q = 0; q < 18; ++q)
+                v[q] = f2(make_float2(offa >= 0 ? st[q * W + offa] : 0.0f, offb >= 0 ? st[q * W + offb] : 0.0f));
+        }
+    };
+
+    auto row_macros = [&](int l, Mac<f2>& m, f2& r, f2& p) -> bool {
+        const int s = l % S;
+        const bool ok = __all_sync(FULL, mbar_wait(&bars[s], (uint32_t)((l / S) & 1)));
+        if (ok && (offa >= 0 || offb >= 0)) {
+            f2 v[18];
+            load_pair(s, v);
+            f2 rd, jx, jy, sg;
+            lbm::node_sums(v, v + 9, rd, jx, jy, sg);
+            lbm::macros(P2, rd, jx, jy, sg, m);
+            r = m.rho_d;
+            p = m.p_d;
+        } else {
+            r = f2(0.0f);
+            p = f2(0.0f);
+        }
+        return ok;
+    };
+
+    for (int l = 0; l < S; ++l) issue(l);
+    int waited = 0;
+    Mac<f2> mc, mn;
+    f2 rm(0.0f), pm(0.0f), r0(0.0f), p0(0.0f), rp(0.0f), pp(0.0f);
+    bool ok = true;
+    if (phys(0) >= 0) ok = row_macros(0, mn, rm, pm);
+    if (ok) {
+        waited = 1;
+        ok = row_macros(1, mc, r0, p0);
+    }
+    if (ok) waited = 2;
+
+    for (int k = 0; ok && k < nrows; ++k) {
+        const int j = w.y0 + k;
+        if (phys(k + 2) >= 0) ok = row_macros(k + 2, mn, rp, pp);
+        if (!ok) break;
+        waited = k + 3;
+        issue(k + S);
+
+        // left neighbour of node a: the previous lane's node b; right
+        // neighbour of node b: the next lane's node a
+        const float rmL = __shfl_up_sync(FULL, rm.v.y, 1), rmR = __shfl_down_sync(FULL, rm.v.x, 1);
+        const float r0L = __shfl_up_sync(FULL, r0.v.y, 1), r0R = __shfl_down_sync(FULL, r0.v.x, 1);
+        const float rpL = __shfl_up_sync(FULL, rp.v.y, 1), rpR = __shfl_down_sync(FULL, rp.v.x, 1);
+        const float pmL = __shfl_up_sync(FULL, pm.v.y, 1), pmR = __shfl_down_sync(FULL, pm.v.x, 1);
+        const float p0L = __shfl_up_sync(FULL, p0.v.y, 1), p0R = __shfl_down_sync(FULL, p0.v.x, 1);
+        const float ppL = __shfl_up_sync(FULL, pp.v.y, 1), ppR = __shfl_down_sync(FULL, pp.v.x, 1);
+        if (act_a) {
+            if (!(isfinite(mc.rho_d.v.x) && isfinite(mc.T_d.v.x)) ||
+                (act_b && !(isfinite(mc.rho_d.v.y) && isfinite(mc.T_d.v.y))))
+                atomicOr(status, 1u);
+            // the stencil for both nodes: left columns (xa - 1, xa), right (xb, xb + 1)
+            auto grad = [&](const f2& cm, const f2& c0, const f2& cp, float mL, float mR, float zL, float zR, float pL,
+                            float pR, f2& gx, f2& gy) {
+                const f2 lm(make_float2(mL, cm.v.x)), rmv(make_float2(cm.v.y, mR));
+                const f2 l0(make_float2(zL, c0.v.x)), r0v(make_float2(c0.v.y, zR));
+                const f2 lp(make_float2(pL, cp.v.x)), rpv(make_float2(cp.v.y, pR));
+                const f2 t(1.0f / 3.0f), d(1.0f / 12.0f);
+                gx = t * (r0v - l0) + d * ((rpv - lp) + (rmv - lm));
+                gy = t * (cp - cm) + d * ((rpv - rmv) + (lp - lm));
+            };
+            f2 grx, gry, gpx, gpy;
+            grad(rm, r0, rp, rmL, rmR, r0L, r0R, rpL, rpR, grx, gry);
+            grad(pm, p0, pp, pmL, pmR, p0L, p0R, ppL, ppR, gpx, gpy);
+            const bool rowwall = !py && (j == 0 || j == ny - 1);
+            const bool colwall = !px && (xa == 0 || xb >= nx - 1);
+            if (rowwall || colwall) {
+                // wall nodes: one-sided second order along the inward normal,
+                // central along the wall (scalar, per node of the pair)
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int x = e ? xb : xa;
+                    if (e && !act_b) break;
+                    const bool onS = !py && j == 0, onN = !py && j == ny - 1;
+                    const bool onW = !px && x == 0, onE = !px && x == nx - 1;
+                    if (!(onS || onN || onW || onE)) continue;
+                    float gr[4];
+#pragma unroll
+                    for (int fld = 0; fld < 2; ++fld) {
+                        const f2& c0f = fld ? p0 : r0;
+                        const f2& cmf = fld ? pm : rm;
+                        const f2& cpf = fld ? pp : rp;
+                        const float v0 = e ? c0f.v.y : c0f.v.x;
+                        // row-j values of the left and right neighbours of this node
+                        const float left = e ? c0f.v.x : (fld ? p0L : r0L);
+                        const float right = e ? (fld ? p0R : r0R) : c0f.v.y;
+                        float gxs, gys;
+                        if (onW || onE) {
+                            const int dx = onW ? 1 : -1;
+                            float r2, p2;
+                            rho_p_at(P1, src, plane, pitch, x + 2 * dx, j, r2, p2);
+                            gxs = (float)dx * (-3.0f * v0 + 4.0f * (onW ? right : left) - (fld ? p2 : r2)) * 0.5f;
+                        } else {
+                            gxs = (right - left) * 0.5f;
+                        }
+                        const float vm = e ? cmf.v.y : cmf.v.x, vp = e ? cpf.v.y : cpf.v.x;
+                        if (onS || onN) {
+                            const int dy = onS ? 1 : -1;
+                            float r2, p2;
+                            rho_p_at(P1, src, plane, pitch, x, j + 2 * dy, r2, p2);
+                            const float v1 = onS ? vp : vm;
+                            gys = (float)dy * (-3.0f * v0 + 4.0f * v1 - (fld ? p2 : r2)) * 0.5f;
+                        } else {
+                            gys = (vp - vm) * 0.5f;
+                        }
+                        gr[2 * fld] = gxs;
+                        gr[2 * fld + 1] = gys;
+                    }
+                    if (e) { grx.v.y = gr[0]; gry.v.y = gr[1]; gpx.v.y = gr[2]; gpy.v.y = gr[3]; }
+                    else { grx.v.x = gr[0]; gry.v.x = gr[1]; gpx.v.x = gr[2]; gpy.v.x = gr[3]; }
+                }
+            }
+
+            f2 v[18];
+            load_pair((k + 1) % S, v);
+            AddDither2 add{mix32(step_hash ^ ((uint32_t)j * 0x85ebca77u + (uint32_t)xa * 0xc2b2ae3du))};
+            lbm::collide(P2, mc, v, v + 9, grx, gry, gpx, gpy, add);
+            push_pair(dst, v, xa, act_b, j, nx, ny, pitch, plane, px, py);
+        }
+        mc = mn;
+        rm = r0; pm = p0;
+        r0 = rp; p0 = pp;
+    }
+    if (!ok) {
+        atomicOr(status, 2u);
+        if (lane == 0)
+            for (int l = waited; l < issued; ++l)
+                if (phys(l) >= 0) mbar_wait(&bars[l % S], (uint32_t)((l / S) & 1));
+        __syncwarp();
     }
 }
 
@@ -1563,8 +1832,10 @@ struct lbm_ctx {
 // pair = 1) or recomputing them at collision time (indices 6-8, pair = 2);
 // one node per thread recomputing the macros, fewer registers (indices 9-11,
 // pair = 3); one autonomous warp per 30 columns, 1, 2 or 4 warps per CTA
-// (indices 12-14, pair = 4).  Variants 3-11 need FP32 storage.
-constexpr int kVariants = 15;
+// (indices 12-14, pair = 4); one autonomous warp per 60 columns, two nodes
+// per lane in packed FP32 (indices 15-17, pair = 5).  Variants 3-11 and
+// 15-17 need FP32 storage.
+constexpr int kVariants = 18;
 
 struct lbm_batch {
     std::vector<lbm_ctx*> ctxs;
@@ -1643,13 +1914,18 @@ void default_shape(const lbm_config& c, int& bx, int& pair) {
 // resident at the same time, shorter ones re-stage more halo rows).
 int batch_rows(const lbm_config& c) { return std::min(c.ny, c.precision == LBM_FP32_DEV ? 32 : 16); }
 
+long long cta_count(const lbm_config& c, int bx, int by) {
+    return (long long)((c.nx + bx - 1) / bx) * ((c.ny + by - 1) / by);
+}
+
 // Rows per run for a lattice launched on its own: the batch length, halved
-// (down to 8) while the lattice gives fewer CTAs than the GPU holds.
-int default_rows(const lbm_config& c, int bx, int resident) {
-    const long long strips = (c.nx + bx - 1) / bx;
-    long long by = batch_rows(c);
-    while (by > 8 && strips * ((c.ny + by - 1) / by) < resident) by /= 2;
-    return (int)std::max<long long>(1, std::min<long long>(by, c.ny));
+// while the lattice gives fewer CTAs than the GPU holds at once (`resident`);
+// small lattices are latency bound, and more, shorter runs spread them over
+// more SMs at the cost of re-staging two halo rows per run.
+int default_rows(const lbm_config& c, int bx, long long resident) {
+    int by = batch_rows(c);
+    while (by > 1 && cta_count(c, bx, by) < resident) by = std::max(1, by / 2);
+    return std::max(1, std::min(by, c.ny));
 }
 
 lbm_status upload_work(lbm_ctx* c) {
@@ -1680,6 +1956,15 @@ cudaError_t configure_warp() {
                                          (int)WarpSmem<R, NW, S>::bytes);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_collide_warp<R, NW, S>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared);
+}
+
+template <int NW>
+cudaError_t configure_warp2() {
+    cudaError_t e = cudaFuncSetAttribute(k_collide_warp2<NW, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Warp2Smem<NW, 3>::bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_collide_warp2<NW, 3>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                 (int)cudaSharedmemCarveoutMaxShared);
 }
 
@@ -1718,9 +2003,70 @@ lbm_status configure_kernels() {
     if (e == cudaSuccess) e = configure_warp<double, 1>();
     if (e == cudaSuccess) e = configure_warp<double, 2>();
     if (e == cudaSuccess) e = configure_warp<double, 4>();
+    if (e == cudaSuccess) e = configure_warp2<1>();
+    if (e == cudaSuccess) e = configure_warp2<2>();
+    if (e == cudaSuccess) e = configure_warp2<4>();
     if (e != cudaSuccess) return fail(LBM_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
     done = 1;
     return LBM_OK;
+}
+
+template <typename K>
+int occupancy_of(K kernel, int threads, size_t smem) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess) n = 1;
+    return std::max(n, 1);
+}
+template <typename R, int BX, bool KEEP>
+int occ_collide() {
+    constexpr int S = FusedTraits<R, BX>::S;
+    return occupancy_of(k_collide_stream<R, BX, S, KEEP>, BX, FusedSmem<R, BX, S>::bytes);
+}
+template <int BX, bool KEEP>
+int occ_pair() { return occupancy_of(k_collide_pair<BX, KEEP>, BX / 2, PairSmem<BX>::bytes); }
+template <typename R, int NW>
+int occ_warp() {
+    constexpr int S = WarpTraits<R>::S;
+    return occupancy_of(k_collide_warp<R, NW, S>, 32 * NW, WarpSmem<R, NW, S>::bytes);
+}
+template <int NW>
+int occ_warp2() { return occupancy_of(k_collide_warp2<NW, 3>, 32 * NW, Warp2Smem<NW, 3>::bytes); }
+
+int variant_per_sm(int vi, bool fp32) {
+    switch (vi) {
+    case 0: return fp32 ? occ_collide<float, 32, true>() : occ_collide<double, 32, true>();
+    case 1: return fp32 ? occ_collide<float, 64, true>() : occ_collide<double, 64, true>();
+    case 3: return occ_pair<64, true>();
+    case 4: return occ_pair<128, true>();
+    case 5: return occ_pair<256, true>();
+    case 6: return occ_pair<64, false>();
+    case 7: return occ_pair<128, false>();
+    case 8: return occ_pair<256, false>();
+    case 9: return occ_collide<float, 32, false>();
+    case 10: return occ_collide<float, 64, false>();
+    case 11: return occ_collide<float, 128, false>();
+    case 12: return fp32 ? occ_warp<float, 1>() : occ_warp<double, 1>();
+    case 13: return fp32 ? occ_warp<float, 2>() : occ_warp<double, 2>();
+    case 14: return fp32 ? occ_warp<float, 4>() : occ_warp<double, 4>();
+    case 15: return occ_warp2<1>();
+    case 16: return occ_warp2<2>();
+    case 17: return occ_warp2<4>();
+    default: return fp32 ? occ_collide<float, 128, true>() : occ_collide<double, 128, true>();
+    }
+}
+
+// CTAs of a variant that the whole GPU holds at once (cached per variant).
+long long resident_ctas(int vi, bool fp32) {
+    static std::mutex mu;
+    static long long cache[2][kVariants] = {{0}};
+    std::lock_guard<std::mutex> g(mu);
+    long long& r = cache[fp32 ? 1 : 0][vi];
+    if (!r) {
+        int dev = 0, sms = 152;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        r = (long long)variant_per_sm(vi, fp32) * std::max(sms, 1);
+    }
+    return r;
 }
 
 template <typename R, int BX, bool KEEP = true>
@@ -1737,14 +2083,22 @@ void launch_warp_nw(const Work* work, int n, InstDesc* const* descs, int par, co
     k_collide_warp<R, NW, S><<<n, 32 * NW, WarpSmem<R, NW, S>::bytes, s>>>(work, descs, par, counter);
 }
 
+template <int NW>
+void launch_warp2_nw(const Work* work, int n, InstDesc* const* descs, int par, const long long* counter,
+                     cudaStream_t s) {
+    constexpr int S = 3;
+    k_collide_warp2<NW, S><<<n, 32 * NW, Warp2Smem<NW, S>::bytes, s>>>(work, descs, par, counter);
+}
+
 template <int BX, bool KEEP>
 void launch_pair_bx(const Work* work, int n, InstDesc* const* descs, int par, const long long* counter,
                     cudaStream_t s) {
     k_collide_pair<BX, KEEP><<<n, BX / 2, PairSmem<BX>::bytes, s>>>(work, descs, par, counter);
 }
 
-static const int kVariantWidth[kVariants] = {32, 64, 128, 64, 128, 256, 64, 128, 256, 32, 64, 128, 30, 60, 120};
-static const int kVariantPair[kVariants] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 4, 4, 4};
+static const int kVariantWidth[kVariants] = {32, 64, 128, 64, 128, 256, 64, 128, 256, 32, 64, 128, 30, 60, 120,
+                                            60, 120, 240};
+static const int kVariantPair[kVariants] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 4, 4, 4, 5, 5, 5};
 
 int variant_index(int bx, int pair) {
     for (int v = 0; v < kVariants; ++v)
@@ -1771,6 +2125,9 @@ void launch_collide(const Work* work, int n, int variant, InstDesc* const* descs
     case 12: launch_warp_nw<R, 1>(work, n, descs, par, counter, s); break;
     case 13: launch_warp_nw<R, 2>(work, n, descs, par, counter, s); break;
     case 14: launch_warp_nw<R, 4>(work, n, descs, par, counter, s); break;
+    case 15: launch_warp2_nw<1>(work, n, descs, par, counter, s); break;
+    case 16: launch_warp2_nw<2>(work, n, descs, par, counter, s); break;
+    case 17: launch_warp2_nw<4>(work, n, descs, par, counter, s); break;
     default: launch_collide_bx<R, 128>(work, n, descs, par, counter, s); break;
     }
 }
@@ -1889,17 +2246,7 @@ lbm_status lbm_create(const lbm_config* cfg, void* workspace, size_t workspace_b
     if (cudaMemcpyAsync(c->d_descs, &p, sizeof(p), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
         return cleanup(fail(LBM_ECUDA, "descs upload"));
     default_shape(*cfg, c->bx, c->pair);
-    {
-        int dev = 0, sms = 152, per_sm = 4;
-        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (cfg->precision == LBM_FP32_DEV)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_collide_warp<float, 1, WarpTraits<float>::S>, 32,
-                                                          WarpSmem<float, 1, WarpTraits<float>::S>::bytes);
-        else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_collide_stream<double, 128, FusedTraits<double, 128>::S, true>,
-                                                          128, FusedSmem<double, 128, FusedTraits<double, 128>::S>::bytes);
-        c->by = default_rows(*cfg, c->bx, sms * std::max(per_sm, 1));
-    }
+    c->by = default_rows(*cfg, c->bx, resident_ctas(variant_index(c->bx, c->pair), is_fp32(c)));
     if ((st = upload_work(c)) != LBM_OK) return cleanup(st);
     c->h_bwork = make_bwork(*cfg, 0, 0);
     ensure_tick(c->h_bwork, 0, 0);
@@ -2053,10 +2400,11 @@ lbm_status lbm_derived(const lbm_ctx* c, double* out8) {
 
 lbm_status lbm_set_tile(lbm_ctx* c, int bx, int by, int pair) {
     if (!c) return fail(LBM_EINVAL, "null ctx");
-    if (pair >= 1 && pair <= 3 && c->cfg.precision != LBM_FP32_DEV)
-        return fail(LBM_EINVAL, "pair 1-3 need FP32 storage");
+    if (pair != 0 && pair != 4 && c->cfg.precision != LBM_FP32_DEV)
+        return fail(LBM_EINVAL, "pair 1-3 and 5 need FP32 storage");
     if (variant_index(bx, pair) < 0)
-        return fail(LBM_EINVAL, pair == 4                ? "warp strips (pair 4) are 30, 60 or 120 columns"
+        return fail(LBM_EINVAL, pair == 4   ? "warp strips (pair 4) are 30, 60 or 120 columns"
+                                : pair == 5 ? "paired warp strips (pair 5) are 60, 120 or 240 columns"
                                 : (pair == 1 || pair == 2) ? "paired strips (pair 1 or 2) are 64, 128 or 256 columns"
                                                            : "bx must be 32, 64 or 128");
     if (by < 1) return fail(LBM_EINVAL, "by must be >= 1");
@@ -2067,6 +2415,14 @@ lbm_status lbm_set_tile(lbm_ctx* c, int bx, int by, int pair) {
     lbm_status st = upload_work(c);
     if (st != LBM_OK) return st;
     CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_get_tile(const lbm_ctx* c, int* bx, int* by, int* pair) {
+    if (!c || !bx || !by || !pair) return fail(LBM_EINVAL, "null argument");
+    *bx = c->bx;
+    *by = c->by;
+    *pair = c->pair;
     return LBM_OK;
 }
 
@@ -2330,6 +2686,23 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, int graph_steps, lbm_ba
     std::vector<InstDesc*> descs;
     std::vector<Work> groups[2][kVariants];
     std::vector<BWork> bgroups[2];
+    // rows per run of the members whose shape was not set: the batch length,
+    // halved for all of them while the batch fills less than the GPU once
+    // (each CTA of a member takes 1 / resident_ctas of the GPU)
+    int shift = 0;
+    for (;; ++shift) {
+        double fill = 0.0;
+        bool can_halve = false;
+        for (int i = 0; i < n; ++i) {
+            const lbm_ctx* c = ctxs[i];
+            if (!c || c->tile_set) continue;
+            const int by = std::max(1, batch_rows(c->cfg) >> shift);
+            can_halve = can_halve || by > 1;
+            fill += (double)cta_count(c->cfg, c->bx, by) /
+                    (double)resident_ctas(variant_index(c->bx, c->pair), c->cfg.precision == LBM_FP32_DEV);
+        }
+        if (fill >= 1.0 || !can_halve) break;
+    }
     for (int i = 0; i < n; ++i) {
         lbm_ctx* c = ctxs[i];
         if (!c || !c->eos_set || c->stream != b->stream || c->sticky != LBM_OK) {
@@ -2340,7 +2713,7 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, int graph_steps, lbm_ba
         descs.push_back(c->d_desc);
         const int pr = is_fp32(c) ? 1 : 0, bi = variant_index(c->bx, c->pair);
         const int par = (int)(c->steps & 1);
-        auto w = make_work(c->cfg, i, c->bx, c->tile_set ? c->by : batch_rows(c->cfg), par, c->steps);
+        auto w = make_work(c->cfg, i, c->bx, c->tile_set ? c->by : std::max(1, batch_rows(c->cfg) >> shift), par, c->steps);
         groups[pr][bi].insert(groups[pr][bi].end(), w.begin(), w.end());
         auto bw = make_bwork(c->cfg, i, par);
         bgroups[pr].insert(bgroups[pr].end(), bw.begin(), bw.end());

@@ -70,7 +70,7 @@ class Config(C.Structure):
 
 EXPORTS = ("lbm_workspace_bytes", "lbm_create", "lbm_set_eos", "lbm_step", "lbm_sync", "lbm_macros",
            "lbm_macros_device", "lbm_nusselt", "lbm_diagnostics", "lbm_get_state", "lbm_set_state",
-           "lbm_init_macros", "lbm_derived", "lbm_set_tile", "lbm_step_count", "lbm_destroy",
+           "lbm_init_macros", "lbm_derived", "lbm_set_tile", "lbm_get_tile", "lbm_step_count", "lbm_destroy",
            "lbm_last_error", "lbm_batch_create", "lbm_batch_step", "lbm_batch_step_profiled",
            "lbm_batch_destroy", "lbm_conserved_sums_static")
 
@@ -100,6 +100,7 @@ def load(path: str | None = None):
         L.lbm_init_macros.argtypes = [vp, dp, dp, dp, dp]
         L.lbm_derived.argtypes = [vp, dp]
         L.lbm_set_tile.argtypes = [vp, i, i, i]
+        L.lbm_get_tile.argtypes = [vp, P(i), P(i), P(i)]
         L.lbm_step_count.argtypes = [vp]
         L.lbm_step_count.restype = C.c_long
         L.lbm_destroy.argtypes = [vp]
@@ -261,6 +262,12 @@ class Lattice:
 
     def set_tile(self, bx: int, by: int, pair: int = 0):
         _check(self.L, self.L.lbm_set_tile(self.h, int(bx), int(by), int(pair)))
+
+    def tile(self) -> tuple:
+        """(bx, by, pair) of the launch shape in use."""
+        bx, by, pr = C.c_int(), C.c_int(), C.c_int()
+        _check(self.L, self.L.lbm_get_tile(self.h, C.byref(bx), C.byref(by), C.byref(pr)))
+        return bx.value, by.value, pr.value
 
     def conserved_sums_static(self, out):
         """Total mass, x and y momentum and sum of g into the device tensor

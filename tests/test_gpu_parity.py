@@ -176,6 +176,40 @@ def test_paired_fp64_rejected(lbm):
     g = lbm.Lattice(W.periodic_box(16, 8))
     for pr in (1, 2, 3):
         assert g.L.lbm_set_tile(g.h, 128, 8, pr) == lbm.LBM_EINVAL
+    assert g.L.lbm_set_tile(g.h, 120, 8, 5) == lbm.LBM_EINVAL
+
+
+@pytest.mark.parametrize("bx,by", [(60, 1), (60, 7), (120, 37), (240, 16)])
+def test_paired_warp_strips_periodic_ragged(orc, lbm, bx, by):
+    # 201 columns: the last pair is half filled and holds the wrapped column 0
+    cfg = W.periodic_box(201, 37, visc_law=2, eos=(W.EOS_CUBIC, (0.05, 0.2)), gamma=1.3,
+                         force=(2e-5, -1e-5), precision=1)
+    _, _, err = pair(orc, lbm, cfg, 100, seed=47, df=1e-4, tile=(bx, by, 5))
+    assert_close(err, TOL32)
+
+
+@pytest.mark.parametrize("nx,ny", [(3, 3), (1, 8), (61, 5), (64, 4)])
+def test_paired_warp_strips_small_periodic(orc, lbm, nx, ny):
+    cfg = W.periodic_box(nx, ny, visc_law=2, eos=(W.EOS_IDEAL, ()), force=(1e-5, -2e-5), precision=1)
+    _, _, err = pair(orc, lbm, cfg, 300, seed=nx * 100 + ny, df=1e-4, tile=(60, 2, 5))
+    assert_close(err, TOL32)
+
+
+@pytest.mark.parametrize("tile", [(60, 16, 5), (120, 7, 5)])
+def test_paired_warp_strips_walls(orc, lbm, tile):
+    # odd side: the east wall column is the first node of a pair
+    cfg = W.cavity(N=67, Ra=1e3, eps=0.6, precision=1)
+    cfg["walls"][1]["u"] = (0.02, 0.0)
+    o, g, err = pair(orc, lbm, cfg, 1500, tile=tile)
+    assert_close(err, TOL32)
+    assert abs(g.nusselt(W.WALL_W) / o.nusselt(W.WALL_W) - 1) < 5e-3
+
+
+def test_paired_warp_strips_even_walls(orc, lbm):
+    # even side: the east wall column is the second node of a pair
+    cfg = W.cavity(N=64, Ra=1e3, eps=0.6, precision=1)
+    _, _, err = pair(orc, lbm, cfg, 1500, tile=(60, 9, 5))
+    assert_close(err, TOL32)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
