@@ -17,6 +17,7 @@
 // (plus one halo column on each side) in a shared-memory ring, so the
 // gradients of the correction terms T grad(rho) and X grad(p) need no extra
 // pass over HBM.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -34,6 +35,7 @@
 
 using lbm::f2;
 using lbm::Mac;
+using lbm::MacC;
 using lbm::Params;
 
 namespace {
@@ -49,7 +51,14 @@ struct WallDev {
     int order;
 };
 
+// Windows staged by one 3-D TMA copy per row in the warp-strip kernels:
+// all 18 planes of kWinCols[k] columns of one row of buffer b, described by
+// tmap[k][b] over the tensor [18][ny][pitch] (k = 0: warp strips, k = 1:
+// paired warp strips, FP32 only).
+constexpr int kWinCols[2] = {36, 68};
+
 struct InstDesc {
+    CUtensorMap tmap[2][2];  // first member: 64-byte aligned with the descriptor
     void* buf[2];
     long long plane;  // elements per plane
     int nx, ny, pitch, px, py;
@@ -119,19 +128,27 @@ __device__ __forceinline__ uint32_t mix32(uint32_t h) {
     return h;
 }
 
+// One draw per node and step: the low 23 bits of the node's hash as the
+// mantissa of a float in [1, 2), mapped to r * 2^-23 with r uniform in
+// [-1/2, 1/2).  Multiplying by 2^e (a stored value with its mantissa
+// cleared) gives r * ulp for normal values and 0 for zero.  Every stored
+// value gets +r or -r (alternating over the links, opposite for f_i and
+// g_i): each is rounded without bias, which is all the update needs; the
+// 18 draws of a node are correlated, not independent.
+__device__ __forceinline__ float dither_draw(uint32_t h) {
+    return fmaf(__int_as_float(0x3f800000u | (h & 0x007fffffu)), 1.1920928955078125e-7f, -1.7881393432617188e-7f);
+}
+__device__ __forceinline__ float ulp_scale(float v) { return __int_as_float(__float_as_int(v) & 0x7f800000); }
+
 struct AddDither {
-    mutable uint32_t h;
-    // f_i and g_i are independent variables, so one uniform draw serves both.
-    // Draw: a Weyl step of the node's hash, its low 23 bits as the mantissa of
-    // a float in [1, 2), mapped to r * 2^-23 with r uniform in [-1/2, 1/2).
-    // Multiplying by 2^e (the stored value with its mantissa cleared) gives
-    // r * ulp for normal values and 0 for zero.
+    float r;
+    mutable float s = 1.0f;  // sign of the next link's draw (folds to a constant once unrolled)
+    __device__ __forceinline__ explicit AddDither(uint32_t h) : r(dither_draw(h)) {}
     __device__ __forceinline__ void operator()(float& f, float df, float& g, float dg) const {
-        h += 0x9e3779b9u;
-        const float r = fmaf(__int_as_float(0x3f800000u | (h & 0x007fffffu)), 1.1920928955078125e-7f,
-                             -1.7881393432617188e-7f);
-        f = f + fmaf(r, __int_as_float(__float_as_int(f) & 0x7f800000), df);
-        g = g + fmaf(r, __int_as_float(__float_as_int(g) & 0x7f800000), dg);
+        const float rs = s * r;
+        f = f + fmaf(rs, ulp_scale(f), df);
+        g = g + fmaf(-rs, ulp_scale(g), dg);
+        s = -s;
     }
     __device__ __forceinline__ void operator()(double& f, double df, double& g, double dg) const {
         f = f + df;
@@ -310,6 +327,18 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                  : "memory");
 }
 
+// One 3-D tensor copy: the box of `tmap` at (x, y, z) into shared memory,
+// completing on an mbarrier.  x * element size must be a multiple of 16
+// bytes; the destination is 128-byte aligned; coordinates outside the
+// tensor read as zero and still count towards the transaction bytes.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tmap, int x, int y, int z, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+            smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+
 // ------------------------------------------------------------------------
 // fused collide + stream
 // ------------------------------------------------------------------------
@@ -425,7 +454,7 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
 
     // wait for logical row l and put its rho', p' into ring slot l % 4;
     // active threads also return their own node's macros in m
-    auto row_macros = [&](int l, Mac<R>& m) -> bool {
+    auto row_macros = [&](int l, MacC<R>& mk) -> bool {
         const int s = l % S;
         if (!mbar_wait(&bars[s], (uint32_t)((l / S) & 1))) {
             atomicOr(status, 2u);
@@ -439,7 +468,9 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
             R v[18];
 #pragma unroll
             for (int q = 0; q < 18; ++q) v[q] = st[q * W + E + tid];
+            Mac<R> m;
             node_macros(P, v, m);
+            compress(m, mk);
             s_rho[slot][c] = m.rho_d;
             s_p[slot][c] = m.p_d;
         }
@@ -463,7 +494,7 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
     };
 
     for (int l = 0; l < S; ++l) issue(l);
-    Mac<R> mc, mn;
+    MacC<R> mc, mn;
     if (phys(0) >= 0) row_macros(0, mn);
     row_macros(1, mc);
 
@@ -524,12 +555,25 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
             const R* st = stage + (size_t)((k + 1) % S) * 18 * W + E + tid;
 #pragma unroll
             for (int q = 0; q < 18; ++q) v[q] = st[q * W];
-            if (!KEEP) {
-                node_macros(P, v, mc);
-                if (!(isfinite(mc.rho_d) && isfinite(mc.T_d))) atomicOr(status, 1u);
+            Mac<R> mf;
+            if (KEEP) {
+                expand(P, mc, mf);
+            } else {
+                node_macros(P, v, mf);
+                if (!(isfinite(mf.rho_d) && isfinite(mf.T_d))) atomicOr(status, 1u);
             }
-            AddDither add{mix32(step_hash ^ ((uint32_t)j * 0x85ebca77u + (uint32_t)x * 0xc2b2ae3du))};
-            lbm::collide(P, mc, v, v + 9, grx, gry, gpx, gpy, add);
+            AddDither add(mix32(step_hash ^ ((uint32_t)j * 0x85ebca77u + (uint32_t)x * 0xc2b2ae3du)));
+            // the DFs are fetched again for the final update, so that they
+            // need not occupy registers through the collision
+            auto reload = [&](R* f, R* g) {
+                asm volatile("" ::: "memory");
+#pragma unroll
+                for (int q = 0; q < 9; ++q) {
+                    f[q] = st[q * W];
+                    g[q] = st[(9 + q) * W];
+                }
+            };
+            lbm::collide(P, mf, v, v + 9, grx, gry, gpx, gpy, add, reload);
 
             push_node(dst, v, x, j, nx, ny, pitch, plane, px, py);
         }
@@ -553,15 +597,17 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
 constexpr int kWarpCols = 30;
 
 // Shared-memory layout of k_collide_warp: per warp, S stages of one lattice
-// row (18 planes, each [MW-element window][left wrap chunk][right wrap chunk])
-// and S mbarriers; then the parameters.  The window starts at the 16-byte
-// boundary at or below column wx0 - 1 and covers up to column wx0 + 30.
+// row and S mbarriers; then the parameters.  A stage holds the window
+// [18 planes][MW columns] that one tensor copy writes, then, for a periodic
+// edge, [18 planes][left wrap chunk, right wrap chunk].  The window starts at
+// the 16-byte boundary at or below column wx0 - 1 and covers up to column
+// wx0 + 30.
 template <typename R, int NW, int S>
 struct WarpSmem {
     static constexpr int E = 16 / (int)sizeof(R);  // elements per 16-byte chunk
-    static constexpr int MW = 36;
-    static constexpr int W = MW + 2 * E;
-    static constexpr size_t stage_bytes = (size_t)18 * W * sizeof(R);
+    static constexpr int MW = kWinCols[0];
+    static constexpr size_t wrap_off = (size_t)18 * MW * sizeof(R);  // bytes
+    static constexpr size_t stage_bytes = (wrap_off + (size_t)18 * 2 * E * sizeof(R) + 127) / 128 * 128;
     static constexpr size_t warp_bytes = (size_t)S * stage_bytes;
     static constexpr size_t off_bars = (size_t)NW * warp_bytes;
     static constexpr size_t off_params = (off_bars + 8 * NW * S + 15) / 16 * 16;
@@ -585,7 +631,7 @@ __global__ void __launch_bounds__(32 * NW, WarpTraits<R>::WARPS_PER_SM / NW)
     k_collide_warp(const Work* __restrict__ work, InstDesc* const* __restrict__ descs, int step_par,
                    const long long* __restrict__ counter) {
     using L = WarpSmem<R, NW, S>;
-    constexpr int E = L::E, MW = L::MW, W = L::W;
+    constexpr int E = L::E, MW = L::MW;
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ __align__(128) unsigned char smem[];
     Params<R>& P = *reinterpret_cast<Params<R>*>(smem + L::off_params);
@@ -594,7 +640,7 @@ __global__ void __launch_bounds__(32 * NW, WarpTraits<R>::WARPS_PER_SM / NW)
     const InstDesc* D = descs[w.inst];
     load_params(&P, &dparams<R>(D));
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    R* stage = reinterpret_cast<R*>(smem + (size_t)wid * L::warp_bytes);
+    unsigned char* wstage = smem + (size_t)wid * L::warp_bytes;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::off_bars) + wid * S;
     if (lane == 0) {
         for (int k = 0; k < S; ++k) mbar_init(&bars[k], 1);
@@ -614,15 +660,18 @@ __global__ void __launch_bounds__(32 * NW, WarpTraits<R>::WARPS_PER_SM / NW)
     const int x = wx0 + lane - 1;  // this lane's column
     const bool owned = lane >= 1 && lane <= kWarpCols && x < nx;
     const int a = (max(wx0 - 1, 0) / E) * E;  // window start (16-byte aligned)
-    const int nmain = min(MW, pitch - a);     // pitch is a multiple of 32 elements
     const bool wrap_l = px && wx0 == 0;                 // lane 0 holds column nx - 1
     const bool wrap_r = px && wx0 + kWarpCols >= nx;    // lane nx - wx0 + 1 holds column 0
     const int cl = ((nx - 1) / E) * E;
-    int off = -1;  // the lane's column in a stage row; -1: no column
+    // the lane's column: window column `off`, or (wrapped) element `off` of
+    // the wrap chunks; off < 0: no column
+    int off = -1;
+    const bool in_wrap = (x == -1 && wrap_l) || (x == nx && wrap_r);
     if (x >= 0 && x < nx) off = x - a;
-    else if (x == -1 && wrap_l) off = MW + (nx - 1 - cl);
-    else if (x == nx && wrap_r) off = MW + E;
-    const uint32_t tx = (uint32_t)(18 * (nmain + (wrap_l ? E : 0) + (wrap_r ? E : 0)) * (int)sizeof(R));
+    else if (x == -1 && wrap_l) off = nx - 1 - cl;
+    else if (x == nx && wrap_r) off = E;
+    const CUtensorMap* tmap = &D->tmap[0][b];
+    const uint32_t tx = (uint32_t)(18 * (MW + (wrap_l ? E : 0) + (wrap_r ? E : 0)) * (int)sizeof(R));
     const int nrows = w.y1 - w.y0;
     const int last_l = nrows + 1;  // logical rows 0..last_l = physical y0-1..y1
 
@@ -648,26 +697,46 @@ __global__ void __launch_bounds__(32 * NW, WarpTraits<R>::WARPS_PER_SM / NW)
             else mbar_arrive_expect_tx(&bars[s], tx);
         }
         __syncwarp();
-        if (y >= 0 && lane < 18) {
-            fence_proxy_async();
-            const R* row = src + lane * plane + (long long)y * pitch;
-            R* st = stage + (size_t)s * 18 * W + (size_t)lane * W;
-            bulk_g2s(st, row + a, (uint32_t)(nmain * sizeof(R)), &bars[s]);
-            if (wrap_l) bulk_g2s(st + MW, row + cl, 16u, &bars[s]);
-            if (wrap_r) bulk_g2s(st + MW + E, row, 16u, &bars[s]);
+        if (y >= 0) {
+            unsigned char* st = wstage + (size_t)s * L::stage_bytes;
+            if (lane == 0) {
+                fence_proxy_async();
+                tma_load_3d(st, tmap, a, y, 0, &bars[s]);
+            }
+            if ((wrap_l || wrap_r) && lane < 18) {
+                fence_proxy_async();
+                const R* row = src + lane * plane + (long long)y * pitch;
+                R* wb = reinterpret_cast<R*>(st + L::wrap_off) + 2 * E * lane;
+                if (wrap_l) bulk_g2s(wb, row + cl, 16u, &bars[s]);
+                if (wrap_r) bulk_g2s(wb + E, row, 16u, &bars[s]);
+            }
+        }
+    };
+
+    // this lane's 18 DFs from stage s
+    auto load_node = [&](int s, R* v) {
+        const unsigned char* st = wstage + (size_t)s * L::stage_bytes;
+        if (!in_wrap) {
+            const R* p = reinterpret_cast<const R*>(st) + off;
+#pragma unroll
+            for (int q = 0; q < 18; ++q) v[q] = p[q * MW];
+        } else {
+            const R* p = reinterpret_cast<const R*>(st + L::wrap_off) + off;
+#pragma unroll
+            for (int q = 0; q < 18; ++q) v[q] = p[q * 2 * E];
         }
     };
 
     // wait for logical row l; lanes holding a column return its macros
-    auto row_macros = [&](int l, Mac<R>& m, R& r, R& p) -> bool {
+    auto row_macros = [&](int l, MacC<R>& mk, R& r, R& p) -> bool {
         const int s = l % S;
         const bool ok = __all_sync(FULL, mbar_wait(&bars[s], (uint32_t)((l / S) & 1)));
         if (ok && off >= 0) {
-            const R* st = stage + (size_t)s * 18 * W + off;
             R v[18];
-#pragma unroll
-            for (int q = 0; q < 18; ++q) v[q] = st[q * W];
+            load_node(s, v);
+            Mac<R> m;
             node_macros(P, v, m);
+            compress(m, mk);
             r = m.rho_d;
             p = m.p_d;
         } else {
@@ -679,7 +748,7 @@ __global__ void __launch_bounds__(32 * NW, WarpTraits<R>::WARPS_PER_SM / NW)
 
     for (int l = 0; l < S; ++l) issue(l);
     int waited = 0;  // logical rows whose copies this warp has waited for
-    Mac<R> mc, mn;
+    MacC<R> mc, mn;
     R rm = R(0), pm = R(0), r0 = R(0), p0 = R(0), rp = R(0), pp = R(0);
     bool ok = true;
     if (phys(0) >= 0) ok = row_macros(0, mn, rm, pm);
@@ -742,11 +811,18 @@ __global__ void __launch_bounds__(32 * NW, WarpTraits<R>::WARPS_PER_SM / NW)
             }
 
             R v[18];
-            const R* st = stage + (size_t)((k + 1) % S) * 18 * W + off;
-#pragma unroll
-            for (int q = 0; q < 18; ++q) v[q] = st[q * W];
-            AddDither add{mix32(step_hash ^ ((uint32_t)j * 0x85ebca77u + (uint32_t)x * 0xc2b2ae3du))};
-            lbm::collide(P, mc, v, v + 9, grx, gry, gpx, gpy, add);
+            const int sc = (k + 1) % S;
+            load_node(sc, v);
+            Mac<R> mf;
+            expand(P, mc, mf);
+            AddDither add(mix32(step_hash ^ ((uint32_t)j * 0x85ebca77u + (uint32_t)x * 0xc2b2ae3du)));
+            // the DFs are fetched again for the final update, so that they
+            // need not occupy registers through the collision
+            auto reload = [&](R* f, R*) {
+                asm volatile("" ::: "memory");
+                load_node(sc, f);  // f and g are v and v + 9: all 18 DFs
+            };
+            lbm::collide(P, mf, v, v + 9, grx, gry, gpx, gpy, add, reload);
             push_node(dst, v, x, j, nx, ny, pitch, plane, px, py);
         }
         mc = mn;
@@ -801,22 +877,18 @@ __device__ void broadcast_params(const Params<float>& a, Params<f2>& b) {
 }
 
 // Stochastic rounding of a pair of nodes: one draw per node and link.
+// The rounding of AddDither for a pair of nodes: one draw per node, from
+// the pair's hash and from its Weyl successor.
 struct AddDither2 {
-    mutable uint32_t h;
-    // the draw of AddDither, one per node of the pair and link
+    float2 r;
+    mutable float s = 1.0f;
+    __device__ __forceinline__ explicit AddDither2(uint32_t h)
+        : r(make_float2(dither_draw(h), dither_draw(h + 0x9e3779b9u))) {}
     __device__ __forceinline__ void operator()(f2& f, f2 df, f2& g, f2 dg) const {
-        const uint32_t ha = h + 0x9e3779b9u, hb = ha + 0x9e3779b9u;
-        h = hb;
-        const float2 r = __ffma2_rn(make_float2(__int_as_float(0x3f800000u | (ha & 0x007fffffu)),
-                                                __int_as_float(0x3f800000u | (hb & 0x007fffffu))),
-                                    make_float2(1.1920928955078125e-7f, 1.1920928955078125e-7f),
-                                    make_float2(-1.7881393432617188e-7f, -1.7881393432617188e-7f));
-        const float2 ef = make_float2(__int_as_float(__float_as_int(f.v.x) & 0x7f800000),
-                                      __int_as_float(__float_as_int(f.v.y) & 0x7f800000));
-        const float2 eg = make_float2(__int_as_float(__float_as_int(g.v.x) & 0x7f800000),
-                                      __int_as_float(__float_as_int(g.v.y) & 0x7f800000));
-        f = f2(__fadd2_rn(f.v, __ffma2_rn(r, ef, df.v)));
-        g = f2(__fadd2_rn(g.v, __ffma2_rn(r, eg, dg.v)));
+        const float2 rs = make_float2(s * r.x, s * r.y), rn = make_float2(-rs.x, -rs.y);
+        f = f2(__fadd2_rn(f.v, __ffma2_rn(rs, make_float2(ulp_scale(f.v.x), ulp_scale(f.v.y)), df.v)));
+        g = f2(__fadd2_rn(g.v, __ffma2_rn(rn, make_float2(ulp_scale(g.v.x), ulp_scale(g.v.y)), dg.v)));
+        s = -s;
     }
 };
 
@@ -901,7 +973,7 @@ __global__ void __launch_bounds__(BX / 2, (KEEP ? 512 : 768) / BX) k_collide_pai
         }
     };
 
-    auto row_macros = [&](int l, Mac<f2>& m) -> bool {
+    auto row_macros = [&](int l, MacC<f2>& mk) -> bool {
         const int s = l % S;
         if (!mbar_wait(&bars[s], (uint32_t)((l / S) & 1))) {
             atomicOr(status, 2u);
@@ -917,7 +989,9 @@ __global__ void __launch_bounds__(BX / 2, (KEEP ? 512 : 768) / BX) k_collide_pai
             for (int q = 0; q < 18; ++q) v[q] = f2(*reinterpret_cast<const float2*>(st + q * W + E + 2 * tid));
             f2 rd, jx, jy, sg;
             lbm::node_sums(v, v + 9, rd, jx, jy, sg);
+            Mac<f2> m;
             lbm::macros(P2, rd, jx, jy, sg, m);
+            compress(m, mk);
             if (act_b) {
                 *reinterpret_cast<float2*>(&s_rho[slot][ca]) = m.rho_d.v;
                 *reinterpret_cast<float2*>(&s_p[slot][ca]) = m.p_d.v;
@@ -947,7 +1021,7 @@ __global__ void __launch_bounds__(BX / 2, (KEEP ? 512 : 768) / BX) k_collide_pai
     };
 
     for (int l = 0; l < S; ++l) issue(l);
-    Mac<f2> mc, mn;
+    MacC<f2> mc, mn;
     if (phys(0) >= 0) row_macros(0, mn);
     row_macros(1, mc);
 
@@ -1024,15 +1098,26 @@ __global__ void __launch_bounds__(BX / 2, (KEEP ? 512 : 768) / BX) k_collide_pai
             const float* st = stage + (size_t)((k + 1) % S) * 18 * W + E + 2 * tid;
 #pragma unroll
             for (int q = 0; q < 18; ++q) v[q] = f2(*reinterpret_cast<const float2*>(st + q * W));
-            if (!KEEP) {
+            Mac<f2> mf;
+            if (KEEP) {
+                expand(P2, mc, mf);
+            } else {
                 f2 rd, jx, jy, sg;
                 lbm::node_sums(v, v + 9, rd, jx, jy, sg);
-                lbm::macros(P2, rd, jx, jy, sg, mc);
+                lbm::macros(P2, rd, jx, jy, sg, mf);
+                if (!(isfinite(mf.rho_d.v.x) && isfinite(mf.T_d.v.x) && (!act_b || (isfinite(mf.rho_d.v.y) && isfinite(mf.T_d.v.y)))))
+                    atomicOr(status, 1u);
             }
-            if (!KEEP && !(isfinite(mc.rho_d.v.x) && isfinite(mc.T_d.v.x) && (!act_b || (isfinite(mc.rho_d.v.y) && isfinite(mc.T_d.v.y)))))
-                atomicOr(status, 1u);
-            AddDither2 add{mix32(step_hash ^ ((uint32_t)j * 0x85ebca77u + (uint32_t)xa * 0xc2b2ae3du))};
-            lbm::collide(P2, mc, v, v + 9, grx, gry, gpx, gpy, add);
+            AddDither2 add(mix32(step_hash ^ ((uint32_t)j * 0x85ebca77u + (uint32_t)xa * 0xc2b2ae3du)));
+            auto reload = [&](f2* f, f2* g) {
+                asm volatile("" ::: "memory");
+#pragma unroll
+                for (int q = 0; q < 9; ++q) {
+                    f[q] = f2(*reinterpret_cast<const float2*>(st + q * W));
+                    g[q] = f2(*reinterpret_cast<const float2*>(st + (9 + q) * W));
+                }
+            };
+            lbm::collide(P2, mf, v, v + 9, grx, gry, gpx, gpy, add, reload);
 
             push_pair(dst, v, xa, act_b, j, nx, ny, pitch, plane, px, py);
         }
@@ -1054,12 +1139,14 @@ __global__ void __launch_bounds__(BX / 2, (KEEP ? 512 : 768) / BX) k_collide_pai
 // second element) and lane 31 column wx0 + 60 (its first element).
 constexpr int kWarp2Cols = 60;
 
+// Stage layout as in WarpSmem, with a window of columns floor4(wx0 - 2) ..
+// floor4(wx0 - 2) + 67.
 template <int NW, int S>
 struct Warp2Smem {
-    static constexpr int E = 4;   // floats per 16-byte chunk
-    static constexpr int MW = 68; // window: columns floor4(wx0 - 2) .. wx0 + 60 and beyond
-    static constexpr int W = MW + 2 * E;
-    static constexpr size_t stage_bytes = (size_t)18 * W * sizeof(float);
+    static constexpr int E = 4;  // floats per 16-byte chunk
+    static constexpr int MW = kWinCols[1];
+    static constexpr size_t wrap_off = (size_t)18 * MW * sizeof(float);
+    static constexpr size_t stage_bytes = (wrap_off + (size_t)18 * 2 * E * sizeof(float) + 127) / 128 * 128;
     static constexpr size_t warp_bytes = (size_t)S * stage_bytes;
     static constexpr size_t off_bars = (size_t)NW * warp_bytes;
     static constexpr size_t off_p2 = (off_bars + 8 * NW * S + 15) / 16 * 16;
@@ -1073,7 +1160,7 @@ struct Warp2Smem {
 // columns.  Neighbour macros come from the lane itself (the other node of
 // its pair) or from the adjacent lane by shuffle.
 #ifndef LBM_WARP2_WARPS_PER_SM
-#define LBM_WARP2_WARPS_PER_SM 8  // resident warps per SM the register budget allows
+#define LBM_WARP2_WARPS_PER_SM 12  // resident warps per SM: 168 registers per thread
 #endif
 
 template <int NW, int S>
@@ -1081,7 +1168,7 @@ __global__ void __launch_bounds__(32 * NW, LBM_WARP2_WARPS_PER_SM / NW)
     k_collide_warp2(const Work* __restrict__ work, InstDesc* const* __restrict__ descs, int step_par,
                     const long long* __restrict__ counter) {
     using L = Warp2Smem<NW, S>;
-    constexpr int E = L::E, MW = L::MW, W = L::W;
+    constexpr int E = L::E, MW = L::MW;
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ __align__(128) unsigned char smem[];
     Params<f2>& P2 = *reinterpret_cast<Params<f2>*>(smem + L::off_p2);
@@ -1091,7 +1178,7 @@ __global__ void __launch_bounds__(32 * NW, LBM_WARP2_WARPS_PER_SM / NW)
     const InstDesc* D = descs[w.inst];
     load_params(&P1, &D->pf);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    float* stage = reinterpret_cast<float*>(smem + (size_t)wid * L::warp_bytes);
+    unsigned char* wstage = smem + (size_t)wid * L::warp_bytes;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::off_bars) + wid * S;
     if (lane == 0) {
         for (int k = 0; k < S; ++k) mbar_init(&bars[k], 1);
@@ -1114,20 +1201,22 @@ __global__ void __launch_bounds__(32 * NW, LBM_WARP2_WARPS_PER_SM / NW)
     const bool own = lane >= 1 && lane <= kWarp2Cols / 2;
     const bool act_a = own && xa < nx, act_b = own && xb < nx;
     const int a0 = (max(wx0 - 2, 0) / E) * E;
-    const int nmain = min(MW, pitch - a0);
     const bool wrap_l = px && wx0 == 0;
     const bool wrap_r = px && wx0 + kWarp2Cols >= nx;
     const int cl = ((nx - 1) / E) * E;
-    // stage offset of column x as seen from this warp, or -1 if not held
+    // where column x sits as seen from this warp: window column o (o < MW),
+    // element o - MW of the wrap chunks (o >= MW), or -1 if not held
     auto offset_of = [&](int x) -> int {
-        if (x >= 0 && x < nx && x >= a0 && x - a0 < nmain) return x - a0;
+        if (x >= 0 && x < nx && x >= a0 && x - a0 < MW) return x - a0;
         if (x == -1 && wrap_l) return MW + (nx - 1 - cl);
         if (x == nx && wrap_r) return MW + E;
         return -1;
     };
     const int offa = offset_of(xa), offb = offset_of(xb);
-    const bool fast = offa >= 0 && offb == offa + 1;  // offa is even: one 8-byte load per plane
-    const uint32_t tx = (uint32_t)(18 * (nmain + (wrap_l ? E : 0) + (wrap_r ? E : 0)) * (int)sizeof(float));
+    // both nodes in the window (offa is even): one 8-byte load per plane
+    const bool fast = offa >= 0 && offa < MW && offb == offa + 1;
+    const CUtensorMap* tmap = &D->tmap[1][b];
+    const uint32_t tx = (uint32_t)(18 * (MW + (wrap_l ? E : 0) + (wrap_r ? E : 0)) * (int)sizeof(float));
     const int nrows = w.y1 - w.y0;
     const int last_l = nrows + 1;
 
@@ -1151,30 +1240,40 @@ __global__ void __launch_bounds__(32 * NW, LBM_WARP2_WARPS_PER_SM / NW)
             else mbar_arrive_expect_tx(&bars[s], tx);
         }
         __syncwarp();
-        if (y >= 0 && lane < 18) {
-            fence_proxy_async();
-            const float* row = src + lane * plane + (long long)y * pitch;
-            float* st = stage + (size_t)s * 18 * W + (size_t)lane * W;
-            bulk_g2s(st, row + a0, (uint32_t)(nmain * sizeof(float)), &bars[s]);
-            if (wrap_l) bulk_g2s(st + MW, row + cl, 16u, &bars[s]);
-            if (wrap_r) bulk_g2s(st + MW + E, row, 16u, &bars[s]);
+        if (y >= 0) {
+            unsigned char* st = wstage + (size_t)s * L::stage_bytes;
+            if (lane == 0) {
+                fence_proxy_async();
+                tma_load_3d(st, tmap, a0, y, 0, &bars[s]);
+            }
+            if ((wrap_l || wrap_r) && lane < 18) {
+                fence_proxy_async();
+                const float* row = src + lane * plane + (long long)y * pitch;
+                float* wb = reinterpret_cast<float*>(st + L::wrap_off) + 2 * E * lane;
+                if (wrap_l) bulk_g2s(wb, row + cl, 16u, &bars[s]);
+                if (wrap_r) bulk_g2s(wb + E, row, 16u, &bars[s]);
+            }
         }
     };
 
     // the lane's two nodes from stage s (a column not held reads as 0)
     auto load_pair = [&](int s, f2* v) {
-        const float* st = stage + (size_t)s * 18 * W;
+        const float* st = reinterpret_cast<const float*>(wstage + (size_t)s * L::stage_bytes);
         if (fast) {
 #pragma unroll
-            for (int q = 0; q < 18; ++q) v[q] = f2(*reinterpret_cast<const float2*>(st + q * W + offa));
+            for (int q = 0; q < 18; ++q) v[q] = f2(*reinterpret_cast<const float2*>(st + q * MW + offa));
         } else {
+            const float* wr = reinterpret_cast<const float*>(wstage + (size_t)s * L::stage_bytes + L::wrap_off);
+            auto elem = [&](int o, int q) -> float {
+                if (o < 0) return 0.0f;
+                return o < MW ? st[q * MW + o] : wr[q * 2 * E + (o - MW)];
+            };
 #pragma unroll
-            for (int q = 0; q < 18; ++q)
-                v[q] = f2(make_float2(offa >= 0 ? st[q * W + offa] : 0.0f, offb >= 0 ? st[q * W + offb] : 0.0f));
+            for (int q = 0; q < 18; ++q) v[q] = f2(make_float2(elem(offa, q), elem(offb, q)));
         }
     };
 
-    auto row_macros = [&](int l, Mac<f2>& m, f2& r, f2& p) -> bool {
+    auto row_macros = [&](int l, MacC<f2>& mk, f2& r, f2& p) -> bool {
         const int s = l % S;
         const bool ok = __all_sync(FULL, mbar_wait(&bars[s], (uint32_t)((l / S) & 1)));
         if (ok && (offa >= 0 || offb >= 0)) {
@@ -1182,7 +1281,9 @@ __global__ void __launch_bounds__(32 * NW, LBM_WARP2_WARPS_PER_SM / NW)
             load_pair(s, v);
             f2 rd, jx, jy, sg;
             lbm::node_sums(v, v + 9, rd, jx, jy, sg);
+            Mac<f2> m;
             lbm::macros(P2, rd, jx, jy, sg, m);
+            compress(m, mk);
             r = m.rho_d;
             p = m.p_d;
         } else {
@@ -1194,7 +1295,7 @@ __global__ void __launch_bounds__(32 * NW, LBM_WARP2_WARPS_PER_SM / NW)
 
     for (int l = 0; l < S; ++l) issue(l);
     int waited = 0;
-    Mac<f2> mc, mn;
+    MacC<f2> mc, mn;
     f2 rm(0.0f), pm(0.0f), r0(0.0f), p0(0.0f), rp(0.0f), pp(0.0f);
     bool ok = true;
     if (phys(0) >= 0) ok = row_macros(0, mn, rm, pm);
@@ -1287,8 +1388,14 @@ __global__ void __launch_bounds__(32 * NW, LBM_WARP2_WARPS_PER_SM / NW)
 
             f2 v[18];
             load_pair((k + 1) % S, v);
-            AddDither2 add{mix32(step_hash ^ ((uint32_t)j * 0x85ebca77u + (uint32_t)xa * 0xc2b2ae3du))};
-            lbm::collide(P2, mc, v, v + 9, grx, gry, gpx, gpy, add);
+            Mac<f2> mf;
+            expand(P2, mc, mf);
+            AddDither2 add(mix32(step_hash ^ ((uint32_t)j * 0x85ebca77u + (uint32_t)xa * 0xc2b2ae3du)));
+            auto reload = [&](f2* f, f2*) {
+                asm volatile("" ::: "memory");
+                load_pair((k + 1) % S, f);  // f and g are v and v + 9: all 18 DFs
+            };
+            lbm::collide(P2, mf, v, v + 9, grx, gry, gpx, gpy, add, reload);
             push_pair(dst, v, xa, act_b, j, nx, ny, pitch, plane, px, py);
         }
         mc = mn;
@@ -1899,20 +2006,26 @@ void ensure_tick(std::vector<BWork>& v, int inst, int par) {
     }
 }
 
-// Default launch shape.  FP32 storage: warp strips (pair 4), one warp per
-// CTA; FP64 storage, whose node update is bound by the FP64 pipe rather than
-// by synchronisation: block strips of 128 columns (pair 0).  Both give the
-// same bits as any other pair-0/pair-4 shape.
+// Default launch shape.  FP32 storage: one warp per CTA, in paired warp
+// strips (pair 5) on lattices of 2048^2 nodes or more, where they are
+// fastest (4096^2: 0.68 ms against 0.76 ms), and in warp strips (pair 4)
+// below, where a 60-column strip wastes more lanes on the ragged last strip
+// and fewer, longer warps leave a small lattice latency-bound (1024^2:
+// 0.080 ms against 0.072 ms).  FP64 storage, whose node update is bound by
+// the FP64 pipe rather than by synchronisation: block strips of 128 columns.
+constexpr long long kPairedMinNodes = 2048LL * 2048LL;
 void default_shape(const lbm_config& c, int& bx, int& pair) {
-    if (c.precision == LBM_FP32_DEV) { bx = 30; pair = 4; }
-    else { bx = 128; pair = 0; }
+    if (c.precision != LBM_FP32_DEV) { bx = 128; pair = 0; }
+    else if ((long long)c.nx * c.ny >= kPairedMinNodes) { bx = 60; pair = 5; }
+    else { bx = 30; pair = 4; }
 }
 
 // Rows per run inside a batch, whose CTAs fill the GPU many times over:
-// runs of about 32 (FP32) or 16 (FP64) rows measured best on 4096^2 and
-// 2048^2 lattices (longer runs lose DRAM and L2 locality between CTAs
-// resident at the same time, shorter ones re-stage more halo rows).
-int batch_rows(const lbm_config& c) { return std::min(c.ny, c.precision == LBM_FP32_DEV ? 32 : 16); }
+// the best run lengths measured on a 4096^2 (FP32) or 2048^2 (FP64)
+// lattice: 16 rows for paired warp strips and block strips, 24 for warp
+// strips (longer runs lose DRAM and L2 locality between CTAs resident at
+// the same time, shorter ones re-stage more halo rows).
+int batch_rows(const lbm_config& c, int pair) { return std::min(c.ny, pair == 4 ? 24 : 16); }
 
 long long cta_count(const lbm_config& c, int bx, int by) {
     return (long long)((c.nx + bx - 1) / bx) * ((c.ny + by - 1) / by);
@@ -1922,10 +2035,55 @@ long long cta_count(const lbm_config& c, int bx, int by) {
 // while the lattice gives fewer CTAs than the GPU holds at once (`resident`);
 // small lattices are latency bound, and more, shorter runs spread them over
 // more SMs at the cost of re-staging two halo rows per run.
-int default_rows(const lbm_config& c, int bx, long long resident) {
-    int by = batch_rows(c);
+int default_rows(const lbm_config& c, int bx, int pair, long long resident) {
+    int by = batch_rows(c, pair);
     while (by > 1 && cta_count(c, bx, by) < resident) by = std::max(1, by / 2);
     return std::max(1, std::min(by, c.ny));
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// Tensor maps of the row windows of the warp-strip kernels over both DF
+// buffers, viewed as the tensor [18 planes][ny rows][pitch columns].
+lbm_status encode_windows(lbm_ctx* c) {
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return fail(LBM_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const bool f32 = c->cfg.precision == LBM_FP32_DEV;
+    const cuuint64_t es = f32 ? 4 : 8;
+    const cuuint64_t dims[3] = {(cuuint64_t)c->L.pitch, (cuuint64_t)c->cfg.ny, 18};
+    const cuuint64_t strides[2] = {(cuuint64_t)c->L.pitch * es, (cuuint64_t)c->L.plane * es};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    memset(c->h.tmap, 0, sizeof(c->h.tmap));
+    for (int k = 0; k < 2; ++k) {
+        if (k == 1 && !f32) continue;  // paired warp strips are FP32 only
+        const cuuint32_t box[3] = {(cuuint32_t)kWinCols[k], 1, 18};
+        for (int b = 0; b < 2; ++b) {
+            const CUresult r = enc(&c->h.tmap[k][b], f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                                   3, c->h.buf[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS)
+                return fail(LBM_ECUDA, "cuTensorMapEncodeTiled failed (code " + std::to_string((int)r) + ")");
+        }
+    }
+    return LBM_OK;
 }
 
 lbm_status upload_work(lbm_ctx* c) {
@@ -2222,6 +2380,10 @@ lbm_status lbm_create(const lbm_config* cfg, void* workspace, size_t workspace_b
     InstDesc& h = c->h;
     h.buf[0] = c->ws + c->L.off_bufA;
     h.buf[1] = c->ws + c->L.off_bufB;
+    if ((st = encode_windows(c)) != LBM_OK) {
+        lbm_destroy(c);
+        return st;
+    }
     h.plane = c->L.plane;
     h.nx = cfg->nx;
     h.ny = cfg->ny;
@@ -2246,7 +2408,7 @@ lbm_status lbm_create(const lbm_config* cfg, void* workspace, size_t workspace_b
     if (cudaMemcpyAsync(c->d_descs, &p, sizeof(p), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
         return cleanup(fail(LBM_ECUDA, "descs upload"));
     default_shape(*cfg, c->bx, c->pair);
-    c->by = default_rows(*cfg, c->bx, resident_ctas(variant_index(c->bx, c->pair), is_fp32(c)));
+    c->by = default_rows(*cfg, c->bx, c->pair, resident_ctas(variant_index(c->bx, c->pair), is_fp32(c)));
     if ((st = upload_work(c)) != LBM_OK) return cleanup(st);
     c->h_bwork = make_bwork(*cfg, 0, 0);
     ensure_tick(c->h_bwork, 0, 0);
@@ -2696,7 +2858,7 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, int graph_steps, lbm_ba
         for (int i = 0; i < n; ++i) {
             const lbm_ctx* c = ctxs[i];
             if (!c || c->tile_set) continue;
-            const int by = std::max(1, batch_rows(c->cfg) >> shift);
+            const int by = std::max(1, batch_rows(c->cfg, c->pair) >> shift);
             can_halve = can_halve || by > 1;
             fill += (double)cta_count(c->cfg, c->bx, by) /
                     (double)resident_ctas(variant_index(c->bx, c->pair), c->cfg.precision == LBM_FP32_DEV);
@@ -2713,7 +2875,7 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, int graph_steps, lbm_ba
         descs.push_back(c->d_desc);
         const int pr = is_fp32(c) ? 1 : 0, bi = variant_index(c->bx, c->pair);
         const int par = (int)(c->steps & 1);
-        auto w = make_work(c->cfg, i, c->bx, c->tile_set ? c->by : std::max(1, batch_rows(c->cfg) >> shift), par, c->steps);
+        auto w = make_work(c->cfg, i, c->bx, c->tile_set ? c->by : std::max(1, batch_rows(c->cfg, c->pair) >> shift), par, c->steps);
         groups[pr][bi].insert(groups[pr][bi].end(), w.begin(), w.end());
         auto bw = make_bwork(c->cfg, i, par);
         bgroups[pr].insert(bgroups[pr].end(), bw.begin(), bw.end());

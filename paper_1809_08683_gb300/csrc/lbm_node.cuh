@@ -76,6 +76,15 @@ struct Mac {
     R rho_d, rho, ir, ux, uy, Fx, Fy, qe, rhoE_d, T_d, T, p_d, eta_d, rhoH;
 };
 
+// The part of Mac that the fused kernels keep in registers from a row's
+// macro pass to its collision; expand() rebuilds the rest with the same
+// operations as macros(), so an expanded state equals the original bit
+// for bit.
+template <typename R>
+struct MacC {
+    R rho_d, ir, ux, uy, rhoE_d, T_d, p_d;
+};
+
 // Carnahan-Starling deviation p - p0 with p = Z(e) rho R T, e = b rho / 4
 // (Eq. EOSs.3).  The density part is differenced in FP64 to avoid
 // cancellation when the arithmetic type is FP32.
@@ -113,24 +122,60 @@ LBM_HD R eos_dev(const Params<R>& P, R rho_d, R rho, R T_d, R T) {
     }
 }
 
+// Body force F = rho g (force_mode 1) or F = g, and q = u . F.
+template <typename R>
+LBM_HD void mac_force(const Params<R>& P, Mac<R>& m) {
+    if (P.force_mode) { m.Fx = m.rho * P.Fx; m.Fy = m.rho * P.Fy; }
+    else { m.Fx = P.Fx; m.Fy = P.Fy; }
+}
+template <typename R>
+LBM_HD void mac_qe(Mac<R>& m) { m.qe = m.ux * m.Fx + m.uy * m.Fy; }
+
+// eta' = (3 p' - (2 + alpha1) rho') / beta1 and rho H - rho0 H0 + p0.
+template <typename R>
+LBM_HD void mac_tail(const Params<R>& P, Mac<R>& m) {
+    m.eta_d = fdiv(R(3) * m.p_d - (R(2) + P.alpha1) * m.rho_d, P.beta1);
+    m.rhoH = P.rho0E0_p0 + m.rhoE_d + m.p_d;
+}
+
 // Eq. (rho.u), Eq. (E), T = eps / Cv, p_EOS, eta = (p / c_s^2 - (2 + alpha1) rho) / beta1.
 template <typename R>
 LBM_HD void macros(const Params<R>& P, R rho_d, R jx, R jy, R sg, Mac<R>& m) {
     m.rho_d = rho_d;
     m.rho = P.rho0 + rho_d;
     m.ir = fdiv(R(1), m.rho);
-    if (P.force_mode) { m.Fx = m.rho * P.Fx; m.Fy = m.rho * P.Fy; }
-    else { m.Fx = P.Fx; m.Fy = P.Fy; }
+    mac_force(P, m);
     m.ux = (jx + R(0.5) * m.Fx) * m.ir;
     m.uy = (jy + R(0.5) * m.Fy) * m.ir;
-    m.qe = m.ux * m.Fx + m.uy * m.Fy;
+    mac_qe(m);
     m.rhoE_d = sg + R(0.5) * m.qe;
     R E_d = (m.rhoE_d - rho_d * P.E0) * m.ir;
     m.T_d = (E_d - R(0.5) * (m.ux * m.ux + m.uy * m.uy)) * P.inv_Cv;
     m.T = P.T0 + m.T_d;
     m.p_d = eos_dev(P, rho_d, m.rho, m.T_d, m.T);
-    m.eta_d = fdiv(R(3) * m.p_d - (R(2) + P.alpha1) * rho_d, P.beta1);
-    m.rhoH = P.rho0E0_p0 + m.rhoE_d + m.p_d;
+    mac_tail(P, m);
+}
+
+template <typename R>
+LBM_HD void compress(const Mac<R>& m, MacC<R>& c) {
+    c.rho_d = m.rho_d; c.ir = m.ir; c.ux = m.ux; c.uy = m.uy;
+    c.rhoE_d = m.rhoE_d; c.T_d = m.T_d; c.p_d = m.p_d;
+}
+
+template <typename R>
+LBM_HD void expand(const Params<R>& P, const MacC<R>& c, Mac<R>& m) {
+    m.rho_d = c.rho_d;
+    m.rho = P.rho0 + c.rho_d;
+    m.ir = c.ir;
+    mac_force(P, m);
+    m.ux = c.ux;
+    m.uy = c.uy;
+    mac_qe(m);
+    m.rhoE_d = c.rhoE_d;
+    m.T_d = c.T_d;
+    m.T = P.T0 + c.T_d;
+    m.p_d = c.p_d;
+    mac_tail(P, m);
 }
 
 // Macros of a wall node whose density, velocity and total energy are fixed
@@ -310,19 +355,29 @@ struct AddNearest {
     }
 };
 
+// Leaves f and g as they are between the moments and the final update.
+struct KeepDFs {
+    template <typename R>
+    LBM_HD void operator()(R*, R*) const {}
+};
+
 // Full collision of one node (Eqs. LBE.u.c, LBE.T.c) in increment form: the
 // moment changes m_bar - m and n_bar - n are formed from small quantities
 // only (force and source moments, non-equilibrium parts, corrections), then
 // mapped back with M^-1 and added to the stored deviations through `add`,
 // which may round stochastically.  f, g hold deviations on entry and the
-// post-collision deviations on exit.
-template <typename R, typename Add>
+// post-collision deviations on exit.  f and g are read twice: for the
+// moments, and for the final update after `reload(f, g)`; a caller that can
+// fetch them again (from shared memory) passes a reload that does so, and
+// the values need not stay in registers through the collision.
+template <typename R, typename Add, typename Reload = KeepDFs>
 LBM_HD void collide(const Params<R>& P, const Mac<R>& mc, R* f, R* g, R grx, R gry, R gpx, R gpy,
-                    const Add& add) {
+                    const Add& add, const Reload& reload = Reload()) {
     Rates<R> r;
     rates(P, mc.ir, mc.T, r);
-    R m[9];
+    R m[9], n[9];
     moments(f, m);
+    moments(g, n);
     Dev<R> d;
     neq_density(P, mc, m[1], m[2], m[4], m[6], m[7], m[8], d);
     Gv<R> G;
@@ -375,8 +430,6 @@ LBM_HD void collide(const Params<R>& P, const Mac<R>& mc, R* f, R* g, R grx, R g
     R Gt1 = G.G1 - R(0.5) * C1, Gt7 = G.G7 - R(0.5) * C7, Gt8 = G.G8 - R(0.5) * C8;
 
     // total-energy DF: n_bar - n = Q - L (n - n^eq + Q/2) + Y ((m + m_bar)/2 - m^eq)
-    R n[9];
-    moments(g, n);
     EDev<R> e;
     energy_eq(P, mc, e);
     R dn1 = n[1] - e.ne1 + R(0.5) * e.Q1;
@@ -402,6 +455,7 @@ LBM_HD void collide(const Params<R>& P, const Mac<R>& mc, R* f, R* g, R grx, R g
     R df[9], dg[9];
     inverse_moments(dm, df);
     inverse_moments(nb, dg);
+    reload(f, g);
 #pragma unroll
     for (int i = 0; i < 9; ++i) add(f[i], df[i], g[i], dg[i]);
 }
