@@ -51,14 +51,17 @@ struct WallDev {
     int order;
 };
 
-// Windows staged by one 3-D TMA copy per row in the warp-strip kernels:
-// all 18 planes of kWinCols[k] columns of one row of buffer b, described by
-// tmap[k][b] over the tensor [18][ny][pitch] (k = 0: warp strips, k = 1:
-// paired warp strips, FP32 only).
+// Windows staged by one 3-D TMA copy per row: all 18 planes of a run of
+// columns of one row of buffer b, described by tmap[k][b] over the tensor
+// [18][ny][pitch].  k = 0: warp strips (kWinCols[0] columns); k = 1: paired
+// warp strips (kWinCols[1], FP32 only); k = 2, 3, 4: block strips of 32, 64,
+// 128 columns with a 16-byte chunk on either side.
 constexpr int kWinCols[2] = {36, 68};
+constexpr int kTmaps = 5;
+__host__ __device__ constexpr int tmap_block_index(int bx) { return bx == 32 ? 2 : (bx == 64 ? 3 : 4); }
 
 struct InstDesc {
-    CUtensorMap tmap[2][2];  // first member: 64-byte aligned with the descriptor
+    CUtensorMap tmap[kTmaps][2];  // first member: 64-byte aligned with the descriptor
     void* buf[2];
     long long plane;  // elements per plane
     int nx, ny, pitch, px, py;
@@ -327,6 +330,15 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                  : "memory");
 }
 
+// Tensor copies need 128-byte aligned shared-memory destinations; a CTA
+// whose dynamic shared memory is not aligned that way reports status bit 4
+// and does nothing (the condition is the same for every thread of the CTA).
+__device__ __forceinline__ bool smem_misaligned(const void* smem, unsigned int* status) {
+    if ((smem_addr(smem) & 127u) == 0) return false;
+    if (threadIdx.x == 0) atomicOr(status, 4u);
+    return true;
+}
+
 // One 3-D tensor copy: the box of `tmap` at (x, y, z) into shared memory,
 // completing on an mbarrier.  x * element size must be a multiple of 16
 // bytes; the destination is 128-byte aligned; coordinates outside the
@@ -351,7 +363,7 @@ template <typename R, int BX, int S>
 struct FusedSmem {
     static constexpr int E = 16 / (int)sizeof(R);  // elements per 16-byte chunk
     static constexpr int W = BX + 2 * E;            // stage row width per plane
-    static constexpr size_t stage_bytes = (size_t)18 * W * sizeof(R);
+    static constexpr size_t stage_bytes = ((size_t)18 * W * sizeof(R) + 127) / 128 * 128;
     static constexpr size_t off_bars = (size_t)S * stage_bytes;
     static constexpr size_t off_params = off_bars + 8 * S;
     static constexpr size_t off_ring = (off_params + sizeof(Params<R>) + 15) / 16 * 16;
@@ -377,6 +389,7 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
                      const long long* __restrict__ counter) {
     using L = FusedSmem<R, BX, S>;
     constexpr int E = L::E, W = L::W;
+    constexpr size_t SST = L::stage_bytes / sizeof(R);  // elements from one stage to the next
     extern __shared__ __align__(128) unsigned char smem[];
     R* stage = reinterpret_cast<R*>(smem);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::off_bars);
@@ -387,6 +400,7 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
 
     const Work w = work[blockIdx.x];
     const InstDesc* D = descs[w.inst];
+    if (smem_misaligned(smem, D->status)) return;
     load_params(&P, &dparams<R>(D));
     const int tid = threadIdx.x;
     if (tid == 0) {
@@ -431,6 +445,13 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
 
     // warp 0 issues the copies of logical row l into stage l % S; a row that
     // does not exist still completes its barrier phase (plain arrive)
+    // a strip whose halo wraps across a periodic edge stages its row with
+    // per-plane copies; any other with one tensor copy of columns
+    // x0 - E .. x0 + BX + E - 1, which lays the stage out the same way
+    const bool wraps = px && (w.x0 == 0 || xhr == 0);
+    const CUtensorMap* tmap = &D->tmap[tmap_block_index(BX)][b];
+    const uint32_t tx = wraps ? (uint32_t)(18 * (nmain * (int)sizeof(R) + 16 * (has_l + has_r)))
+                              : (uint32_t)(18 * W * (int)sizeof(R));
     int issued = 0, waited = 0;  // logical rows issued / waited for by this thread
     auto issue = [&](int l) {
         if (l > last_l || tid >= 32) return;
@@ -439,13 +460,18 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
         const int y = phys(l);
         if (tid == 0) {
             if (y < 0) mbar_arrive(&bars[s]);
-            else mbar_arrive_expect_tx(&bars[s], (uint32_t)(18 * (nmain * (int)sizeof(R) + 16 * (has_l + has_r))));
+            else mbar_arrive_expect_tx(&bars[s], tx);
         }
         __syncwarp();
-        if (y >= 0 && tid < 18) {
+        if (y >= 0 && !wraps) {
+            if (tid == 0) {
+                fence_proxy_async();
+                tma_load_3d(stage + (size_t)s * SST, tmap, w.x0 - E, y, 0, &bars[s]);
+            }
+        } else if (y >= 0 && tid < 18) {
             fence_proxy_async();
             const R* row = src + tid * plane + (long long)y * pitch;
-            R* st = stage + (size_t)s * 18 * W + (size_t)tid * W;
+            R* st = stage + (size_t)s * SST + (size_t)tid * W;
             bulk_g2s(st + E, row + w.x0, (uint32_t)(nmain * sizeof(R)), &bars[s]);
             if (has_l) bulk_g2s(st, row + xcl, 16u, &bars[s]);
             if (has_r) bulk_g2s(st + E + BX, row + xcr, 16u, &bars[s]);
@@ -462,7 +488,7 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
             return false;
         }
         waited = l + 1;
-        const R* st = stage + (size_t)s * 18 * W;
+        const R* st = stage + (size_t)s * SST;
         const int slot = l & 3;
         if (active) {
             R v[18];
@@ -552,7 +578,7 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
             }
 
             R v[18];
-            const R* st = stage + (size_t)((k + 1) % S) * 18 * W + E + tid;
+            const R* st = stage + (size_t)((k + 1) % S) * SST + E + tid;
 #pragma unroll
             for (int q = 0; q < 18; ++q) v[q] = st[q * W];
             Mac<R> mf;
@@ -638,6 +664,7 @@ __global__ void __launch_bounds__(32 * NW, WarpTraits<R>::WARPS_PER_SM / NW)
 
     const Work w = work[blockIdx.x];
     const InstDesc* D = descs[w.inst];
+    if (smem_misaligned(smem, D->status)) return;
     load_params(&P, &dparams<R>(D));
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned char* wstage = smem + (size_t)wid * L::warp_bytes;
@@ -1176,6 +1203,7 @@ __global__ void __launch_bounds__(32 * NW, LBM_WARP2_WARPS_PER_SM / NW)
 
     const Work w = work[blockIdx.x];
     const InstDesc* D = descs[w.inst];
+    if (smem_misaligned(smem, D->status)) return;
     load_params(&P1, &D->pf);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned char* wstage = smem + (size_t)wid * L::warp_bytes;
@@ -2070,10 +2098,12 @@ lbm_status encode_windows(lbm_ctx* c) {
     const cuuint64_t dims[3] = {(cuuint64_t)c->L.pitch, (cuuint64_t)c->cfg.ny, 18};
     const cuuint64_t strides[2] = {(cuuint64_t)c->L.pitch * es, (cuuint64_t)c->L.plane * es};
     const cuuint32_t estr[3] = {1, 1, 1};
+    const int E = (int)(16 / es);
     memset(c->h.tmap, 0, sizeof(c->h.tmap));
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < kTmaps; ++k) {
         if (k == 1 && !f32) continue;  // paired warp strips are FP32 only
-        const cuuint32_t box[3] = {(cuuint32_t)kWinCols[k], 1, 18};
+        const int width = k < 2 ? kWinCols[k] : (32 << (k - 2)) + 2 * E;
+        const cuuint32_t box[3] = {(cuuint32_t)width, 1, 18};
         for (int b = 0; b < 2; ++b) {
             const CUresult r = enc(&c->h.tmap[k][b], f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
                                    3, c->h.buf[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -2312,6 +2342,10 @@ lbm_status read_status(lbm_ctx* c) {
     unsigned int st = 0;
     CUDA_TRY(cudaMemcpyAsync(&st, c->d_status, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (st & 4u) {
+        c->sticky = LBM_ECUDA;
+        return fail(LBM_ECUDA, "dynamic shared memory of the fused kernel is not 128-byte aligned");
+    }
     if (st & 2u) {
         c->sticky = LBM_ETIMEOUT;
         return fail(LBM_ETIMEOUT, "a bounded wait on a bulk copy gave up");
