@@ -158,12 +158,12 @@ lbm_status lbm_derived(const lbm_ctx* ctx, double* out8);
 lbm_status lbm_set_tile(lbm_ctx* ctx, int bx, int by, int pair);
 
 /* Launch shape in use: the default chosen by lbm_create or the one set by
- * lbm_set_tile.  Defaults: FP32 storage, paired warp strips (pair = 5,
- * bx = 60) from 2048^2 nodes up, else warp strips (pair = 4, bx = 30);
- * FP64 storage, block strips (pair = 0, bx = 128); by from the lattice size
- * and the GPU's occupancy.  by is the run length when the lattice is
- * stepped alone; a batch shortens the runs of members whose shape was not
- * set until it fills the GPU. */
+ * lbm_set_tile.  Default: block strips, pair = 0, bx = 128, or warp strips,
+ * pair = 4, bx = 30, for nx <= 160 (same results); by = ny / 128 between 1
+ * and 24 (FP32) or 8 (FP64).  by is
+ * the run length when the lattice is stepped alone; a batch uses runs of
+ * up to 24 (FP32) or 8 (FP64) rows for members whose shape was not set,
+ * shortened until the batch fills the GPU. */
 lbm_status lbm_get_tile(const lbm_ctx* ctx, int* bx, int* by, int* pair);
 
 /* Steps taken since the last (re)initialisation. */

@@ -878,11 +878,11 @@ __global__ void __launch_bounds__(32 * NW, WarpTraits<R>::WARPS_PER_SM / NW)
 // pairs, and populations that stream along y only are stored as pairs.
 template <int BX>
 struct PairSmem {
-    static constexpr int S = 4;
+    static constexpr int S = 3;
     static constexpr int E = 4;              // floats per 16-byte halo chunk
     static constexpr int W = BX + 2 * E;
     static constexpr int RW = BX + 4;        // ring row: x - x0 + 2, halos at 1 and (xlast - x0) + 3
-    static constexpr size_t stage_bytes = (size_t)18 * W * sizeof(float);
+    static constexpr size_t stage_bytes = ((size_t)18 * W * sizeof(float) + 127) / 128 * 128;
     static constexpr size_t off_bars = (size_t)S * stage_bytes;
     static constexpr size_t off_p2 = (off_bars + 8 * S + 15) / 16 * 16;
     static constexpr size_t off_p1 = (off_p2 + sizeof(Params<f2>) + 15) / 16 * 16;
@@ -919,12 +919,17 @@ struct AddDither2 {
     }
 };
 
+#ifndef LBM_PAIR_WARPS_PER_SM
+#define LBM_PAIR_WARPS_PER_SM 12  // resident warps per SM with the row macros kept in registers
+#endif
+
 template <int BX, bool KEEP>
-__global__ void __launch_bounds__(BX / 2, (KEEP ? 512 : 768) / BX) k_collide_pair(const Work* __restrict__ work,
+__global__ void __launch_bounds__(BX / 2, (KEEP ? LBM_PAIR_WARPS_PER_SM : 12) * 64 / BX) k_collide_pair(const Work* __restrict__ work,
                                                                     InstDesc* const* __restrict__ descs,
                                                                     int step_par, const long long* __restrict__ counter) {
     using L = PairSmem<BX>;
     constexpr int E = L::E, W = L::W, S = L::S, RW = L::RW;
+    constexpr size_t SST = L::stage_bytes / sizeof(float);  // floats from one stage to the next
     extern __shared__ __align__(128) unsigned char smem[];
     float* stage = reinterpret_cast<float*>(smem);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::off_bars);
@@ -936,6 +941,7 @@ __global__ void __launch_bounds__(BX / 2, (KEEP ? 512 : 768) / BX) k_collide_pai
 
     const Work w = work[blockIdx.x];
     const InstDesc* D = descs[w.inst];
+    if (smem_misaligned(smem, D->status)) return;
     load_params(&P1, &D->pf);
     const int tid = threadIdx.x;
     if (tid == 0) {
@@ -979,6 +985,12 @@ __global__ void __launch_bounds__(BX / 2, (KEEP ? 512 : 768) / BX) k_collide_pai
         return y;
     };
 
+    // one tensor copy per row unless the halo wraps across a periodic edge
+    // (a window of more than 256 columns takes per-plane copies too)
+    constexpr bool kTensor = BX + 2 * E <= 256;
+    const bool wraps = !kTensor || (px && (w.x0 == 0 || xhr == 0));
+    const CUtensorMap* tmap = &D->tmap[tmap_block_index(kTensor ? BX : 128)][b];
+    const uint32_t tx = wraps ? (uint32_t)(18 * (nmain * 4 + 16 * (has_l + has_r))) : (uint32_t)(18 * W * 4);
     int issued = 0, waited = 0;  // logical rows issued / waited for by this thread
     auto issue = [&](int l) {
         if (l > last_l || tid >= 32) return;
@@ -987,13 +999,18 @@ __global__ void __launch_bounds__(BX / 2, (KEEP ? 512 : 768) / BX) k_collide_pai
         const int y = phys(l);
         if (tid == 0) {
             if (y < 0) mbar_arrive(&bars[s]);
-            else mbar_arrive_expect_tx(&bars[s], (uint32_t)(18 * (nmain * 4 + 16 * (has_l + has_r))));
+            else mbar_arrive_expect_tx(&bars[s], tx);
         }
         __syncwarp();
-        if (y >= 0 && tid < 18) {
+        if (y >= 0 && !wraps) {
+            if (tid == 0) {
+                fence_proxy_async();
+                tma_load_3d(stage + (size_t)s * SST, tmap, w.x0 - E, y, 0, &bars[s]);
+            }
+        } else if (y >= 0 && tid < 18) {
             fence_proxy_async();
             const float* row = src + tid * plane + (long long)y * pitch;
-            float* st = stage + (size_t)s * 18 * W + (size_t)tid * W;
+            float* st = stage + (size_t)s * SST + (size_t)tid * W;
             bulk_g2s(st + E, row + w.x0, (uint32_t)(nmain * 4), &bars[s]);
             if (has_l) bulk_g2s(st, row + xcl, 16u, &bars[s]);
             if (has_r) bulk_g2s(st + E + BX, row + xcr, 16u, &bars[s]);
@@ -1008,7 +1025,7 @@ __global__ void __launch_bounds__(BX / 2, (KEEP ? 512 : 768) / BX) k_collide_pai
             return false;
         }
         waited = l + 1;
-        const float* st = stage + (size_t)s * 18 * W;
+        const float* st = stage + (size_t)s * SST;
         const int slot = l & 3;
         if (act_a) {
             f2 v[18];
@@ -1122,7 +1139,7 @@ __global__ void __launch_bounds__(BX / 2, (KEEP ? 512 : 768) / BX) k_collide_pai
             }
 
             f2 v[18];
-            const float* st = stage + (size_t)((k + 1) % S) * 18 * W + E + 2 * tid;
+            const float* st = stage + (size_t)((k + 1) % S) * SST + E + 2 * tid;
 #pragma unroll
             for (int q = 0; q < 18; ++q) v[q] = f2(*reinterpret_cast<const float2*>(st + q * W));
             Mac<f2> mf;
@@ -2034,39 +2051,40 @@ void ensure_tick(std::vector<BWork>& v, int inst, int par) {
     }
 }
 
-// Default launch shape.  FP32 storage: one warp per CTA, in paired warp
-// strips (pair 5) on lattices of 2048^2 nodes or more, where they are
-// fastest (4096^2: 0.68 ms against 0.76 ms), and in warp strips (pair 4)
-// below, where a 60-column strip wastes more lanes on the ragged last strip
-// and fewer, longer warps leave a small lattice latency-bound (1024^2:
-// 0.080 ms against 0.072 ms).  FP64 storage, whose node update is bound by
-// the FP64 pipe rather than by synchronisation: block strips of 128 columns.
-constexpr long long kPairedMinNodes = 2048LL * 2048LL;
+// Default launch shape: block strips of 128 columns (pair 0), which with
+// each row staged by one tensor copy measured fastest on every square FP32
+// lattice from 512^2 to 4096^2 (4096^2: 0.58 ms against 0.62 ms for paired
+// and 0.63 ms for plain warp strips) and on the 96-cavity batch (one launch
+// for all members beats narrower strips for the ragged ones); FP64 is bound
+// by the FP64 pipe and prefers them too.  Lattices up to 160 columns wide
+// take warp strips of 30 columns (pair 4, same bits as pair 0): they waste
+// fewer lanes there and give small lattices more CTAs.
 void default_shape(const lbm_config& c, int& bx, int& pair) {
-    if (c.precision != LBM_FP32_DEV) { bx = 128; pair = 0; }
-    else if ((long long)c.nx * c.ny >= kPairedMinNodes) { bx = 60; pair = 5; }
-    else { bx = 30; pair = 4; }
+    if (c.nx <= 160) { bx = 30; pair = 4; }
+    else { bx = 128; pair = 0; }
 }
 
-// Rows per run inside a batch, whose CTAs fill the GPU many times over:
-// the best run lengths measured on a 4096^2 (FP32) or 2048^2 (FP64)
-// lattice: 16 rows for paired warp strips and block strips, 24 for warp
-// strips (longer runs lose DRAM and L2 locality between CTAs resident at
-// the same time, shorter ones re-stage more halo rows).
-int batch_rows(const lbm_config& c, int pair) { return std::min(c.ny, pair == 4 ? 24 : 16); }
+// Longest run of rows per CTA: the best measured on a 4096^2 (FP32) or
+// 2048^2 (FP64) lattice and on the 96-cavity batch (longer runs lose DRAM
+// and L2 locality between CTAs resident at the same time, shorter ones
+// re-stage more halo rows).
+int batch_rows(const lbm_config& c, int pair) {
+    const bool f32 = c.precision == LBM_FP32_DEV;
+    const int by = pair == 0 ? (f32 ? 24 : 8) : (pair == 5 ? 16 : 24);
+    return std::min(c.ny, by);
+}
 
 long long cta_count(const lbm_config& c, int bx, int by) {
     return (long long)((c.nx + bx - 1) / bx) * ((c.ny + by - 1) / by);
 }
 
-// Rows per run for a lattice launched on its own: the batch length, halved
-// while the lattice gives fewer CTAs than the GPU holds at once (`resident`);
-// small lattices are latency bound, and more, shorter runs spread them over
-// more SMs at the cost of re-staging two halo rows per run.
-int default_rows(const lbm_config& c, int bx, int pair, long long resident) {
-    int by = batch_rows(c, pair);
-    while (by > 1 && cta_count(c, bx, by) < resident) by = std::max(1, by / 2);
-    return std::max(1, std::min(by, c.ny));
+// Rows per run for a lattice launched on its own: ny / 128, between 1 and
+// the longest run.  Measured optimum on square FP32 lattices: 1-2 rows at
+// 256^2, 4 at 512^2, 8 at 1024^2, 12-16 at 2048^2, 24 at 4096^2; a small
+// lattice is latency-bound and gains more from spreading over more SMs than
+// it loses re-staging halo rows.
+int default_rows(const lbm_config& c, int pair) {
+    return std::max(1, std::min(batch_rows(c, pair), c.ny / 128));
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -2442,7 +2460,7 @@ lbm_status lbm_create(const lbm_config* cfg, void* workspace, size_t workspace_b
     if (cudaMemcpyAsync(c->d_descs, &p, sizeof(p), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
         return cleanup(fail(LBM_ECUDA, "descs upload"));
     default_shape(*cfg, c->bx, c->pair);
-    c->by = default_rows(*cfg, c->bx, c->pair, resident_ctas(variant_index(c->bx, c->pair), is_fp32(c)));
+    c->by = default_rows(*cfg, c->pair);
     if ((st = upload_work(c)) != LBM_OK) return cleanup(st);
     c->h_bwork = make_bwork(*cfg, 0, 0);
     ensure_tick(c->h_bwork, 0, 0);
