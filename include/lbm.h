@@ -173,9 +173,15 @@ lbm_status lbm_destroy(lbm_ctx* ctx);            /* NULL-safe */
 const char* lbm_last_error(void);
 
 /* Batched stepping: contexts (same stream, any size/EOS/precision mix) are
- * advanced together, one fused launch per precision and one wall-pass launch
- * per step.  graph_steps > 0 captures that many steps in a CUDA graph that
- * lbm_batch_step replays (nsteps must then be a multiple of graph_steps). */
+ * advanced together, one fused launch per group of members sharing a
+ * precision, launch shape and model class (lattices of 32768 nodes or more
+ * with the heated-cavity model, ideal or cubic EOS, run a specialised
+ * kernel instance, all others the generic one) and one wall-pass launch per
+ * precision per step.  A lattice gives the same bits alone or batched.
+ * graph_steps > 0 captures that many steps in a CUDA graph that
+ * lbm_batch_step replays (nsteps must then be a multiple of graph_steps).
+ * A member whose EOS class lbm_set_eos changes afterwards makes the batch
+ * step fail with LBM_EINVAL: build the batch again. */
 lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, int graph_steps, lbm_batch** out);
 lbm_status lbm_batch_step(lbm_batch* b, long nsteps);
 lbm_status lbm_batch_destroy(lbm_batch* b);     /* NULL-safe */

@@ -73,7 +73,8 @@ struct InstDesc {
 };
 
 struct Work {  // one CTA of the fused kernel
-    int inst, x0, y0, y1, par, pad0;
+    int inst, x0, y0, y1, par;
+    int dir;          // block strips: 0 sweeps the run upwards (+y), 1 downwards
     long long step0;  // the lattice's step count when this table was built
 };
 
@@ -101,11 +102,11 @@ __device__ __forceinline__ void store18(R* __restrict__ base, long long plane, l
     for (int q = 0; q < 18; ++q) base[q * plane + idx] = v[q];
 }
 
-template <typename R>
+template <int MC = lbm::MODEL_ANY, typename R>
 __device__ __forceinline__ void node_macros(const Params<R>& P, const R* v, Mac<R>& m) {
     R rd, jx, jy, sg;
     lbm::node_sums(v, v + 9, rd, jx, jy, sg);
-    lbm::macros(P, rd, jx, jy, sg, m);
+    lbm::macros<MC>(P, rd, jx, jy, sg, m);
 }
 
 template <typename R>
@@ -160,13 +161,13 @@ struct AddDither {
 };
 
 // rho' and p' of node (xx, yy) read straight from a buffer.
-template <typename R>
+template <int MC = lbm::MODEL_ANY, typename R>
 __device__ void rho_p_at(const Params<R>& P, const R* __restrict__ src, long long plane, int pitch,
                          int xx, int yy, R& rd, R& pd) {
     R v[18];
     load18(src, plane, (long long)yy * pitch + xx, v);
     Mac<R> m;
-    node_macros(P, v, m);
+    node_macros<MC>(P, v, m);
     rd = m.rho_d;
     pd = m.p_d;
 }
@@ -355,6 +356,13 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tmap, 
 // fused collide + stream
 // ------------------------------------------------------------------------
 
+// rho' and p' of one node, adjacent so that the gradient stencil reads both
+// with one shared-memory load.
+template <typename R>
+struct alignas(2 * sizeof(R)) RhoP {
+    R r, p;
+};
+
 // Shared-memory layout of the fused kernel: S stages of one lattice row of
 // the CTA's strip (18 planes, each [16-byte left-halo chunk][BX][16-byte
 // right-halo chunk]), one mbarrier per stage, the parameters, and a 4-row
@@ -383,7 +391,7 @@ struct FusedTraits {
 // KEEP = true carries each thread's macros from the row pass to the
 // collision; KEEP = false recomputes them from the staged DFs, trading about
 // 50 instructions per node for fewer registers and more resident warps.
-template <typename R, int BX, int S, bool KEEP = true>
+template <typename R, int BX, int S, bool KEEP = true, int MC = lbm::MODEL_ANY>
 __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTraits<R, BX>::MINB_LEAN)
     k_collide_stream(const Work* __restrict__ work, InstDesc* const* __restrict__ descs, int step_par,
                      const long long* __restrict__ counter) {
@@ -394,8 +402,7 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
     R* stage = reinterpret_cast<R*>(smem);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::off_bars);
     Params<R>& P = *reinterpret_cast<Params<R>*>(smem + L::off_params);
-    R(*s_rho)[BX + 2] = reinterpret_cast<R(*)[BX + 2]>(smem + L::off_ring);
-    R(*s_p)[BX + 2] = s_rho + 4;
+    RhoP<R>(*s_rp)[BX + 2] = reinterpret_cast<RhoP<R>(*)[BX + 2]>(smem + L::off_ring);
     __shared__ int s_abort;
 
     const Work w = work[blockIdx.x];
@@ -430,12 +437,16 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
     const int xcl = has_l ? (xhl / E) * E : 0, xcr = has_r ? (xhr / E) * E : 0;
     const int nmain = min(BX, pitch - w.x0);  // multiple of 32 elements: 16-byte sized
     const int nrows = w.y1 - w.y0;
-    const int last_l = nrows + 1;             // logical rows 0..last_l = physical y0-1..y1
-    const int c = tid + 1;
+    const int last_l = nrows + 1;             // logical rows 0..last_l = physical y0-1..y1 (dir 0)
+    const int c = tid + 1;                    //                         or y1..y0-1 (dir 1)
+    // Vertically adjacent runs sweep in opposite directions, so that the
+    // rows they share (each one's halo rows) are read by both at about the
+    // same time, the second time from L2.
+    const bool down = w.dir != 0;
 
     // physical row of logical row l, or -1 if it lies outside a walled lattice
     auto phys = [&](int l) -> int {
-        int y = w.y0 - 1 + l;
+        int y = down ? w.y1 - l : w.y0 - 1 + l;
         if (y < 0 || y >= ny) {
             if (!py) return -1;
             y = (y < 0) ? y + ny : y - ny;
@@ -495,10 +506,9 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
 #pragma unroll
             for (int q = 0; q < 18; ++q) v[q] = st[q * W + E + tid];
             Mac<R> m;
-            node_macros(P, v, m);
+            node_macros<MC>(P, v, m);
             compress(m, mk);
-            s_rho[slot][c] = m.rho_d;
-            s_p[slot][c] = m.p_d;
+            s_rp[slot][c] = RhoP<R>{m.rho_d, m.p_d};
         }
         // the two halo columns: two adjacent lanes of one warp run the same
         // instruction stream on their own chunk, in warp 1 (not the warp
@@ -512,9 +522,8 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
 #pragma unroll
             for (int q = 0; q < 18; ++q) v[q] = st[q * W + off];
             Mac<R> h;
-            node_macros(P, v, h);
-            s_rho[slot][col] = h.rho_d;
-            s_p[slot][col] = h.p_d;
+            node_macros<MC>(P, v, h);
+            s_rp[slot][col] = RhoP<R>{h.rho_d, h.p_d};
         }
         return true;
     };
@@ -525,7 +534,7 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
     row_macros(1, mc);
 
     for (int k = 0; k < nrows; ++k) {
-        const int j = w.y0 + k;
+        const int j = down ? w.y1 - 1 - k : w.y0 + k;
         if (phys(k + 2) >= 0) row_macros(k + 2, mn);
         __syncthreads();
         if (s_abort) break;
@@ -533,47 +542,47 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
 
         if (active) {
             if (KEEP && !(isfinite(mc.rho_d) && isfinite(mc.T_d))) atomicOr(status, 1u);
-            const int sm = k & 3, s0 = (k + 1) & 3, sp = (k + 2) & 3;
+            // ring slots of the rows j - 1 (sm), j, j + 1 (sp)
+            const int sm = (down ? k + 2 : k) & 3, s0 = (k + 1) & 3, sp = (down ? k : k + 2) & 3;
             const bool onS = !py && j == 0, onN = !py && j == ny - 1;
             const bool onW = !px && x == 0, onE = !px && x == nx - 1;
             R grx, gry, gpx, gpy;
             if (!(onS || onN || onW || onE)) {
                 // grad = 3 sum_i w_i e_i phi(x + e_i), w = 1/9 (axis), 1/36 (diagonal)
                 const R t = R(1.0 / 3.0), d = R(1.0 / 12.0);
-                grx = t * (s_rho[s0][c + 1] - s_rho[s0][c - 1])
-                    + d * ((s_rho[sp][c + 1] - s_rho[sp][c - 1]) + (s_rho[sm][c + 1] - s_rho[sm][c - 1]));
-                gry = t * (s_rho[sp][c] - s_rho[sm][c])
-                    + d * ((s_rho[sp][c + 1] - s_rho[sm][c + 1]) + (s_rho[sp][c - 1] - s_rho[sm][c - 1]));
-                gpx = t * (s_p[s0][c + 1] - s_p[s0][c - 1])
-                    + d * ((s_p[sp][c + 1] - s_p[sp][c - 1]) + (s_p[sm][c + 1] - s_p[sm][c - 1]));
-                gpy = t * (s_p[sp][c] - s_p[sm][c])
-                    + d * ((s_p[sp][c + 1] - s_p[sm][c + 1]) + (s_p[sp][c - 1] - s_p[sm][c - 1]));
+                const RhoP<R> ml = s_rp[sm][c - 1], mc_ = s_rp[sm][c], mr = s_rp[sm][c + 1];
+                const RhoP<R> zl = s_rp[s0][c - 1], zr = s_rp[s0][c + 1];
+                const RhoP<R> pl = s_rp[sp][c - 1], pc = s_rp[sp][c], pr = s_rp[sp][c + 1];
+                grx = t * (zr.r - zl.r) + d * ((pr.r - pl.r) + (mr.r - ml.r));
+                gry = t * (pc.r - mc_.r) + d * ((pr.r - mr.r) + (pl.r - ml.r));
+                gpx = t * (zr.p - zl.p) + d * ((pr.p - pl.p) + (mr.p - ml.p));
+                gpy = t * (pc.p - mc_.p) + d * ((pr.p - mr.p) + (pl.p - ml.p));
             } else {
                 // wall node: one-sided second order along the inward normal,
                 // central along the wall
-                const R r0 = s_rho[s0][c], p0 = s_p[s0][c];
+                const R r0 = s_rp[s0][c].r, p0 = s_rp[s0][c].p;
                 if (onW || onE) {
                     const int dx = onW ? 1 : -1;
                     R r2, p2;
-                    rho_p_at(P, src, plane, pitch, x + 2 * dx, j, r2, p2);
-                    const R r1 = s_rho[s0][c + dx], p1 = s_p[s0][c + dx];
+                    rho_p_at<MC>(P, src, plane, pitch, x + 2 * dx, j, r2, p2);
+                    const R r1 = s_rp[s0][c + dx].r, p1 = s_rp[s0][c + dx].p;
                     grx = R(dx) * (R(-3) * r0 + R(4) * r1 - r2) * R(0.5);
                     gpx = R(dx) * (R(-3) * p0 + R(4) * p1 - p2) * R(0.5);
                 } else {
-                    grx = (s_rho[s0][c + 1] - s_rho[s0][c - 1]) * R(0.5);
-                    gpx = (s_p[s0][c + 1] - s_p[s0][c - 1]) * R(0.5);
+                    grx = (s_rp[s0][c + 1].r - s_rp[s0][c - 1].r) * R(0.5);
+                    gpx = (s_rp[s0][c + 1].p - s_rp[s0][c - 1].p) * R(0.5);
                 }
                 if (onS || onN) {
                     const int dy = onS ? 1 : -1;
                     R r2, p2;
-                    rho_p_at(P, src, plane, pitch, x, j + 2 * dy, r2, p2);
-                    const R r1 = onS ? s_rho[sp][c] : s_rho[sm][c];
-                    const R p1 = onS ? s_p[sp][c] : s_p[sm][c];
+                    rho_p_at<MC>(P, src, plane, pitch, x, j + 2 * dy, r2, p2);
+                    const R r1 = onS ? s_rp[sp][c].r : s_rp[sm][c].r;
+                    const R p1 = onS ? s_rp[sp][c].p : s_rp[sm][c].p;
                     gry = R(dy) * (R(-3) * r0 + R(4) * r1 - r2) * R(0.5);
                     gpy = R(dy) * (R(-3) * p0 + R(4) * p1 - p2) * R(0.5);
                 } else {
-                    gry = (s_rho[sp][c] - s_rho[sm][c]) * R(0.5);
-                    gpy = (s_p[sp][c] - s_p[sm][c]) * R(0.5);
+                    gry = (s_rp[sp][c].r - s_rp[sm][c].r) * R(0.5);
+                    gpy = (s_rp[sp][c].p - s_rp[sm][c].p) * R(0.5);
                 }
             }
 
@@ -583,9 +592,9 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
             for (int q = 0; q < 18; ++q) v[q] = st[q * W];
             Mac<R> mf;
             if (KEEP) {
-                expand(P, mc, mf);
+                lbm::expand<MC>(P, mc, mf);
             } else {
-                node_macros(P, v, mf);
+                node_macros<MC>(P, v, mf);
                 if (!(isfinite(mf.rho_d) && isfinite(mf.T_d))) atomicOr(status, 1u);
             }
             AddDither add(mix32(step_hash ^ ((uint32_t)j * 0x85ebca77u + (uint32_t)x * 0xc2b2ae3du)));
@@ -599,7 +608,7 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
                     g[q] = st[(9 + q) * W];
                 }
             };
-            lbm::collide(P, mf, v, v + 9, grx, gry, gpx, gpy, add, reload);
+            lbm::collide<MC>(P, mf, v, v + 9, grx, gry, gpx, gpy, add, reload);
 
             push_node(dst, v, x, j, nx, ny, pitch, plane, px, py);
         }
@@ -652,7 +661,7 @@ struct WarpTraits {
 // ring of stages, and takes the macros of the neighbouring columns from the
 // neighbouring lanes (warp shuffles) and those of the rows j - 1, j, j + 1
 // from its own registers.  Warps of a CTA only share the parameters.
-template <typename R, int NW, int S>
+template <typename R, int NW, int S, int MC = lbm::MODEL_ANY>
 __global__ void __launch_bounds__(32 * NW, WarpTraits<R>::WARPS_PER_SM / NW)
     k_collide_warp(const Work* __restrict__ work, InstDesc* const* __restrict__ descs, int step_par,
                    const long long* __restrict__ counter) {
@@ -762,7 +771,7 @@ __global__ void __launch_bounds__(32 * NW, WarpTraits<R>::WARPS_PER_SM / NW)
             R v[18];
             load_node(s, v);
             Mac<R> m;
-            node_macros(P, v, m);
+            node_macros<MC>(P, v, m);
             compress(m, mk);
             r = m.rho_d;
             p = m.p_d;
@@ -816,7 +825,7 @@ __global__ void __launch_bounds__(32 * NW, WarpTraits<R>::WARPS_PER_SM / NW)
                 if (onW || onE) {
                     const int dx = onW ? 1 : -1;
                     R r2, p2;
-                    rho_p_at(P, src, plane, pitch, x + 2 * dx, j, r2, p2);
+                    rho_p_at<MC>(P, src, plane, pitch, x + 2 * dx, j, r2, p2);
                     const R r1 = onW ? r0r : r0l, p1 = onW ? p0r : p0l;
                     grx = R(dx) * (R(-3) * r0 + R(4) * r1 - r2) * R(0.5);
                     gpx = R(dx) * (R(-3) * p0 + R(4) * p1 - p2) * R(0.5);
@@ -827,7 +836,7 @@ __global__ void __launch_bounds__(32 * NW, WarpTraits<R>::WARPS_PER_SM / NW)
                 if (onS || onN) {
                     const int dy = onS ? 1 : -1;
                     R r2, p2;
-                    rho_p_at(P, src, plane, pitch, x, j + 2 * dy, r2, p2);
+                    rho_p_at<MC>(P, src, plane, pitch, x, j + 2 * dy, r2, p2);
                     const R r1 = onS ? rp : rm, p1 = onS ? pp : pm;
                     gry = R(dy) * (R(-3) * r0 + R(4) * r1 - r2) * R(0.5);
                     gpy = R(dy) * (R(-3) * p0 + R(4) * p1 - p2) * R(0.5);
@@ -841,7 +850,7 @@ __global__ void __launch_bounds__(32 * NW, WarpTraits<R>::WARPS_PER_SM / NW)
             const int sc = (k + 1) % S;
             load_node(sc, v);
             Mac<R> mf;
-            expand(P, mc, mf);
+            lbm::expand<MC>(P, mc, mf);
             AddDither add(mix32(step_hash ^ ((uint32_t)j * 0x85ebca77u + (uint32_t)x * 0xc2b2ae3du)));
             // the DFs are fetched again for the final update, so that they
             // need not occupy registers through the collision
@@ -849,7 +858,7 @@ __global__ void __launch_bounds__(32 * NW, WarpTraits<R>::WARPS_PER_SM / NW)
                 asm volatile("" ::: "memory");
                 load_node(sc, f);  // f and g are v and v + 9: all 18 DFs
             };
-            lbm::collide(P, mf, v, v + 9, grx, gry, gpx, gpy, add, reload);
+            lbm::collide<MC>(P, mf, v, v + 9, grx, gry, gpx, gpy, add, reload);
             push_node(dst, v, x, j, nx, ny, pitch, plane, px, py);
         }
         mc = mn;
@@ -1967,6 +1976,7 @@ struct lbm_ctx {
     Work* d_work = nullptr;
     int n_work = 0, bx = 128, by = 0, pair = 0;
     bool tile_set = false;  // launch shape chosen by lbm_set_tile, kept in batches
+    int mc = 0;             // model class of the fused kernel (lbm::MODEL_*), set with the EOS
     BWork* d_bwork = nullptr;
     int n_bwork = 0;
     long steps = 0;
@@ -1988,15 +1998,21 @@ struct lbm_ctx {
 // per lane in packed FP32 (indices 15-17, pair = 5).  Variants 3-11 and
 // 15-17 need FP32 storage.
 constexpr int kVariants = 18;
+constexpr int kModels = 2;  // model classes: lbm::MODEL_ANY, lbm::MODEL_CAVITY
+// Lattices below this many nodes keep the generic instance even with the
+// cavity model: they are latency-bound, and batches of them (the serving
+// mix) then stay one launch per shape.
+constexpr long long kModelMinNodes = 32768;
 
 struct lbm_batch {
     std::vector<lbm_ctx*> ctxs;
+    std::vector<int> models;  // each member's model class when the launch groups were built
     cudaStream_t stream = nullptr;
     InstDesc** d_descs = nullptr;
     Work* d_work = nullptr;
     BWork* d_bwork = nullptr;
-    // launch groups: [precision][bx index] ranges of d_work; [precision] ranges of d_bwork
-    int w_off[2][kVariants] = {{0}}, w_cnt[2][kVariants] = {{0}};
+    // launch groups: [precision][variant][model class] ranges of d_work; [precision] ranges of d_bwork
+    int w_off[2][kVariants][kModels] = {}, w_cnt[2][kVariants][kModels] = {};
     int b_off[2] = {0, 0}, b_cnt[2] = {0, 0};
     long steps = 0;
     int graph_steps = 0;
@@ -2019,6 +2035,7 @@ std::vector<Work> make_work(const lbm_config& c, int inst, int bx, int by, int p
             w.y0 = (int)(r * c.ny / nruns);
             w.y1 = (int)((r + 1) * c.ny / nruns);
             w.par = par;
+            w.dir = (int)(r & 1);
             w.step0 = step0;
             v.push_back(w);
         }
@@ -2144,25 +2161,40 @@ lbm_status upload_work(lbm_ctx* c) {
     return LBM_OK;
 }
 
-template <typename R, int BX, bool KEEP = true>
+template <typename R, int BX, bool KEEP = true, int MC = lbm::MODEL_ANY>
 cudaError_t configure_collide() {
     constexpr int S = FusedTraits<R, BX>::S;
-    cudaError_t e = cudaFuncSetAttribute(k_collide_stream<R, BX, S, KEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)FusedSmem<R, BX, S>::bytes);
+    cudaError_t e = cudaFuncSetAttribute(k_collide_stream<R, BX, S, KEEP, MC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FusedSmem<R, BX, S>::bytes);
     if (e != cudaSuccess) return e;
     // prefer shared memory over L1: the row stages, not L1, feed the kernel
-    return cudaFuncSetAttribute(k_collide_stream<R, BX, S, KEEP>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    return cudaFuncSetAttribute(k_collide_stream<R, BX, S, KEEP, MC>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                 (int)cudaSharedmemCarveoutMaxShared);
 }
 
-template <typename R, int NW>
+template <typename R, int NW, int MC = lbm::MODEL_ANY>
 cudaError_t configure_warp() {
     constexpr int S = WarpTraits<R>::S;
-    cudaError_t e = cudaFuncSetAttribute(k_collide_warp<R, NW, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_collide_warp<R, NW, S, MC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)WarpSmem<R, NW, S>::bytes);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_collide_warp<R, NW, S>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    return cudaFuncSetAttribute(k_collide_warp<R, NW, S, MC>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                 (int)cudaSharedmemCarveoutMaxShared);
+}
+
+template <typename R, int MC>
+cudaError_t configure_model() {
+    cudaError_t e = configure_collide<R, 32, true, MC>();
+    if (e == cudaSuccess) e = configure_collide<R, 64, true, MC>();
+    if (e == cudaSuccess) e = configure_collide<R, 128, true, MC>();
+    if (e == cudaSuccess) e = configure_warp<R, 1, MC>();
+    if (e == cudaSuccess) e = configure_warp<R, 2, MC>();
+    if (e == cudaSuccess) e = configure_warp<R, 4, MC>();
+    return e;
+}
+template <typename R>
+cudaError_t configure_models() {
+    return configure_model<R, lbm::MODEL_CAVITY>();
 }
 
 template <int NW>
@@ -2209,6 +2241,9 @@ lbm_status configure_kernels() {
     if (e == cudaSuccess) e = configure_warp<double, 1>();
     if (e == cudaSuccess) e = configure_warp<double, 2>();
     if (e == cudaSuccess) e = configure_warp<double, 4>();
+    // the one-node-per-thread shapes, specialised for the heated-cavity models
+    if (e == cudaSuccess) e = configure_models<float>();
+    if (e == cudaSuccess) e = configure_models<double>();
     if (e == cudaSuccess) e = configure_warp2<1>();
     if (e == cudaSuccess) e = configure_warp2<2>();
     if (e == cudaSuccess) e = configure_warp2<4>();
@@ -2275,18 +2310,18 @@ long long resident_ctas(int vi, bool fp32) {
     return r;
 }
 
-template <typename R, int BX, bool KEEP = true>
+template <typename R, int BX, bool KEEP = true, int MC = lbm::MODEL_ANY>
 void launch_collide_bx(const Work* work, int n, InstDesc* const* descs, int par, const long long* counter,
                        cudaStream_t s) {
     constexpr int S = FusedTraits<R, BX>::S;
-    k_collide_stream<R, BX, S, KEEP><<<n, BX, FusedSmem<R, BX, S>::bytes, s>>>(work, descs, par, counter);
+    k_collide_stream<R, BX, S, KEEP, MC><<<n, BX, FusedSmem<R, BX, S>::bytes, s>>>(work, descs, par, counter);
 }
 
-template <typename R, int NW>
+template <typename R, int NW, int MC = lbm::MODEL_ANY>
 void launch_warp_nw(const Work* work, int n, InstDesc* const* descs, int par, const long long* counter,
                     cudaStream_t s) {
     constexpr int S = WarpTraits<R>::S;
-    k_collide_warp<R, NW, S><<<n, 32 * NW, WarpSmem<R, NW, S>::bytes, s>>>(work, descs, par, counter);
+    k_collide_warp<R, NW, S, MC><<<n, 32 * NW, WarpSmem<R, NW, S>::bytes, s>>>(work, descs, par, counter);
 }
 
 template <int NW>
@@ -2312,10 +2347,36 @@ int variant_index(int bx, int pair) {
     return -1;
 }
 
+// Model class a launch of `variant` can use: the one-node-per-thread shapes
+// that keep the row macros (block strips, variants 0-2; warp strips,
+// variants 12-14) have instances specialised for the heated-cavity model,
+// so that all of them still give the same bits for a lattice; every other
+// shape runs the generic instance.
+int launch_model(int variant, int mc) {
+    return (variant <= 2 || (variant >= 12 && variant <= 14)) ? mc : lbm::MODEL_ANY;
+}
+
+template <typename R, int MC>
+void launch_model_variant(const Work* work, int n, int variant, InstDesc* const* descs, int par,
+                          const long long* counter, cudaStream_t s) {
+    switch (variant) {
+    case 0: launch_collide_bx<R, 32, true, MC>(work, n, descs, par, counter, s); break;
+    case 1: launch_collide_bx<R, 64, true, MC>(work, n, descs, par, counter, s); break;
+    case 2: launch_collide_bx<R, 128, true, MC>(work, n, descs, par, counter, s); break;
+    case 12: launch_warp_nw<R, 1, MC>(work, n, descs, par, counter, s); break;
+    case 13: launch_warp_nw<R, 2, MC>(work, n, descs, par, counter, s); break;
+    default: launch_warp_nw<R, 4, MC>(work, n, descs, par, counter, s); break;
+    }
+}
+
 template <typename R>
-void launch_collide(const Work* work, int n, int variant, InstDesc* const* descs, int par, const long long* counter,
-                    cudaStream_t s) {
+void launch_collide(const Work* work, int n, int variant, int mc, InstDesc* const* descs, int par,
+                    const long long* counter, cudaStream_t s) {
     if (n <= 0) return;
+    if (launch_model(variant, mc) == lbm::MODEL_CAVITY) {
+        launch_model_variant<R, lbm::MODEL_CAVITY>(work, n, variant, descs, par, counter, s);
+        return;
+    }
     switch (variant) {
     case 0: launch_collide_bx<R, 32>(work, n, descs, par, counter, s); break;
     case 1: launch_collide_bx<R, 64>(work, n, descs, par, counter, s); break;
@@ -2573,6 +2634,10 @@ lbm_status lbm_set_eos(lbm_ctx* c, int kind, const double* params, int np) {
     P.visc = k.visc_law;
     P.force_mode = k.force_mode;
     P.corrections = k.corrections;
+    c->mc = (k.visc_law == 2 && k.force_mode == 1 && k.corrections && (kind == lbm::EOS_IDEAL || kind == lbm::EOS_CUBIC) &&
+             (long long)k.nx * k.ny >= kModelMinNodes)
+                ? lbm::MODEL_CAVITY
+                : lbm::MODEL_ANY;
     c->h.pd = P;
     convert_params(P, c->h.pf);
 
@@ -2652,10 +2717,10 @@ lbm_status lbm_step(lbm_ctx* c, long nsteps) {
     for (long s = 0; s < nsteps; ++s) {
         const int par = (int)((c->steps + s) & 1);
         if (is_fp32(c)) {
-            launch_collide<float>(c->d_work, c->n_work, variant_index(c->bx, c->pair), c->d_descs, par, c->d_counter, c->stream);
+            launch_collide<float>(c->d_work, c->n_work, variant_index(c->bx, c->pair), c->mc, c->d_descs, par, c->d_counter, c->stream);
             launch_boundary<float>(c->d_bwork, c->n_bwork, c->d_descs, par, c->d_counter, c->stream);
         } else {
-            launch_collide<double>(c->d_work, c->n_work, variant_index(c->bx, c->pair), c->d_descs, par, c->d_counter, c->stream);
+            launch_collide<double>(c->d_work, c->n_work, variant_index(c->bx, c->pair), c->mc, c->d_descs, par, c->d_counter, c->stream);
             launch_boundary<double>(c->d_bwork, c->n_bwork, c->d_descs, par, c->d_counter, c->stream);
         }
     }
@@ -2861,13 +2926,14 @@ lbm_status lbm_conserved_sums_static(const lbm_ctx* c, double* out4) {
 
 static void batch_launch_collide(lbm_batch* b, int par) {
     for (int pr = 0; pr < 2; ++pr)
-        for (int vi = 0; vi < kVariants; ++vi) {
-            if (!b->w_cnt[pr][vi]) continue;
-            if (pr)
-                launch_collide<float>(b->d_work + b->w_off[pr][vi], b->w_cnt[pr][vi], vi, b->d_descs, par, b->d_counter, b->stream);
-            else
-                launch_collide<double>(b->d_work + b->w_off[pr][vi], b->w_cnt[pr][vi], vi, b->d_descs, par, b->d_counter, b->stream);
-        }
+        for (int vi = 0; vi < kVariants; ++vi)
+            for (int mc = 0; mc < kModels; ++mc) {
+                const int n = b->w_cnt[pr][vi][mc];
+                if (!n) continue;
+                const Work* w = b->d_work + b->w_off[pr][vi][mc];
+                if (pr) launch_collide<float>(w, n, vi, mc, b->d_descs, par, b->d_counter, b->stream);
+                else launch_collide<double>(w, n, vi, mc, b->d_descs, par, b->d_counter, b->stream);
+            }
 }
 
 static void batch_launch_boundary(lbm_batch* b, int par) {
@@ -2898,7 +2964,7 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, int graph_steps, lbm_ba
     lbm_batch* b = new lbm_batch();
     b->stream = ctxs[0]->stream;
     std::vector<InstDesc*> descs;
-    std::vector<Work> groups[2][kVariants];
+    std::vector<Work> groups[2][kVariants][kModels];
     std::vector<BWork> bgroups[2];
     // rows per run of the members whose shape was not set: the batch length,
     // halved for all of them while the batch fills less than the GPU once
@@ -2924,11 +2990,13 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, int graph_steps, lbm_ba
             return fail(LBM_EINVAL, "batch members must be initialised, stable and share one stream");
         }
         b->ctxs.push_back(c);
+        b->models.push_back(c->mc);
         descs.push_back(c->d_desc);
         const int pr = is_fp32(c) ? 1 : 0, bi = variant_index(c->bx, c->pair);
         const int par = (int)(c->steps & 1);
         auto w = make_work(c->cfg, i, c->bx, c->tile_set ? c->by : std::max(1, batch_rows(c->cfg, c->pair) >> shift), par, c->steps);
-        groups[pr][bi].insert(groups[pr][bi].end(), w.begin(), w.end());
+        auto& grp = groups[pr][bi][launch_model(bi, c->mc)];
+        grp.insert(grp.end(), w.begin(), w.end());
         auto bw = make_bwork(c->cfg, i, par);
         bgroups[pr].insert(bgroups[pr].end(), bw.begin(), bw.end());
     }
@@ -2936,14 +3004,16 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, int graph_steps, lbm_ba
     // longest runs first within each launch, so that short ones fill the tail
     for (int pr = 0; pr < 2; ++pr)
         for (int bi = 0; bi < kVariants; ++bi)
-            std::stable_sort(groups[pr][bi].begin(), groups[pr][bi].end(),
-                             [](const Work& a, const Work& b) { return a.y1 - a.y0 > b.y1 - b.y0; });
+            for (int mc = 0; mc < kModels; ++mc)
+                std::stable_sort(groups[pr][bi][mc].begin(), groups[pr][bi][mc].end(),
+                                 [](const Work& a, const Work& b) { return a.y1 - a.y0 > b.y1 - b.y0; });
     for (int pr = 0; pr < 2; ++pr)
-        for (int bi = 0; bi < kVariants; ++bi) {
-            b->w_off[pr][bi] = (int)all.size();
-            b->w_cnt[pr][bi] = (int)groups[pr][bi].size();
-            all.insert(all.end(), groups[pr][bi].begin(), groups[pr][bi].end());
-        }
+        for (int bi = 0; bi < kVariants; ++bi)
+            for (int mc = 0; mc < kModels; ++mc) {
+                b->w_off[pr][bi][mc] = (int)all.size();
+                b->w_cnt[pr][bi][mc] = (int)groups[pr][bi][mc].size();
+                all.insert(all.end(), groups[pr][bi][mc].begin(), groups[pr][bi][mc].end());
+            }
     if (bgroups[0].empty() && bgroups[1].empty()) ensure_tick(bgroups[is_fp32(ctxs[0]) ? 1 : 0], 0, (int)(ctxs[0]->steps & 1));
     std::vector<BWork> ball;
     for (int pr = 0; pr < 2; ++pr) {
@@ -2987,8 +3057,11 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, int graph_steps, lbm_ba
 
 lbm_status lbm_batch_step(lbm_batch* b, long nsteps) {
     if (!b || nsteps < 0) return fail(LBM_EINVAL, "bad batch step");
-    for (lbm_ctx* c : b->ctxs)
-        if (c->sticky != LBM_OK) return fail(c->sticky, "a batch member is unstable");
+    for (size_t i = 0; i < b->ctxs.size(); ++i) {
+        if (b->ctxs[i]->sticky != LBM_OK) return fail(b->ctxs[i]->sticky, "a batch member is unstable");
+        if (b->ctxs[i]->mc != b->models[i])
+            return fail(LBM_EINVAL, "a batch member's EOS class changed since the batch was built; build it again");
+    }
     if (nsteps == 0) return LBM_OK;
     lbm_status cs = batch_set_counter(b);
     if (cs != LBM_OK) return cs;
@@ -3007,8 +3080,11 @@ lbm_status lbm_batch_step(lbm_batch* b, long nsteps) {
 
 lbm_status lbm_batch_step_profiled(lbm_batch* b, long nsteps, double* ms_collide, double* ms_wall) {
     if (!b || nsteps < 1 || nsteps > 100000 || !ms_collide || !ms_wall) return fail(LBM_EINVAL, "bad profiled step");
-    for (lbm_ctx* c : b->ctxs)
-        if (c->sticky != LBM_OK) return fail(c->sticky, "a batch member is unstable");
+    for (size_t i = 0; i < b->ctxs.size(); ++i) {
+        if (b->ctxs[i]->sticky != LBM_OK) return fail(b->ctxs[i]->sticky, "a batch member is unstable");
+        if (b->ctxs[i]->mc != b->models[i])
+            return fail(LBM_EINVAL, "a batch member's EOS class changed since the batch was built; build it again");
+    }
     std::vector<cudaEvent_t> ev((size_t)3 * nsteps, nullptr);
     auto cleanup = [&]() {
         for (cudaEvent_t e : ev)

@@ -70,6 +70,20 @@ struct Params {
 
 enum { EOS_DECOUPLING = 0, EOS_IDEAL = 1, EOS_CS = 2, EOS_CUBIC = 3 };
 
+// Model classes.  MODEL_ANY reads the EOS, the viscosity law, the force
+// mode and the corrections flag from the parameters at run time.
+// MODEL_CAVITY fixes the heated-cavity model at compile time (Sutherland
+// viscosity, F = rho g, corrections on) and keeps only the ideal-gas and
+// cubic EOS, chosen at run time.  The arithmetic is the same; a fixed model
+// drops the branches and the code of the others.
+enum { MODEL_ANY = 0, MODEL_CAVITY = 1 };
+template <int MC, typename R>
+LBM_HD int visc_law(const Params<R>& P) { return MC != MODEL_ANY ? 2 : P.visc; }
+template <int MC, typename R>
+LBM_HD bool force_is_rho_g(const Params<R>& P) { return MC != MODEL_ANY || P.force_mode != 0; }
+template <int MC, typename R>
+LBM_HD bool corrections_on(const Params<R>& P) { return MC != MODEL_ANY || P.corrections != 0; }
+
 // Macroscopic state of one node in deviation form.
 template <typename R>
 struct Mac {
@@ -103,9 +117,11 @@ LBM_HD float cs_dev(float b, float rho0, float Rg, float rho_d, float T, float T
 }
 
 // p_EOS(rho, T) - p0.
-template <typename R>
+template <int MC = MODEL_ANY, typename R>
 LBM_HD R eos_dev(const Params<R>& P, R rho_d, R rho, R T_d, R T) {
-    switch (P.eos) {
+    const int kind = MC == MODEL_CAVITY ? (P.eos == EOS_CUBIC ? EOS_CUBIC : EOS_IDEAL) : P.eos;
+    if (MC == MODEL_CAVITY && kind == EOS_IDEAL) return P.Rg * (rho_d * T + P.rho0 * T_d);
+    switch (kind) {
     case EOS_DECOUPLING:
         return P.Rg * P.T0 * rho_d;
     case EOS_IDEAL:
@@ -123,9 +139,9 @@ LBM_HD R eos_dev(const Params<R>& P, R rho_d, R rho, R T_d, R T) {
 }
 
 // Body force F = rho g (force_mode 1) or F = g, and q = u . F.
-template <typename R>
+template <int MC = MODEL_ANY, typename R>
 LBM_HD void mac_force(const Params<R>& P, Mac<R>& m) {
-    if (P.force_mode) { m.Fx = m.rho * P.Fx; m.Fy = m.rho * P.Fy; }
+    if (force_is_rho_g<MC>(P)) { m.Fx = m.rho * P.Fx; m.Fy = m.rho * P.Fy; }
     else { m.Fx = P.Fx; m.Fy = P.Fy; }
 }
 template <typename R>
@@ -139,12 +155,12 @@ LBM_HD void mac_tail(const Params<R>& P, Mac<R>& m) {
 }
 
 // Eq. (rho.u), Eq. (E), T = eps / Cv, p_EOS, eta = (p / c_s^2 - (2 + alpha1) rho) / beta1.
-template <typename R>
+template <int MC = MODEL_ANY, typename R>
 LBM_HD void macros(const Params<R>& P, R rho_d, R jx, R jy, R sg, Mac<R>& m) {
     m.rho_d = rho_d;
     m.rho = P.rho0 + rho_d;
     m.ir = fdiv(R(1), m.rho);
-    mac_force(P, m);
+    mac_force<MC>(P, m);
     m.ux = (jx + R(0.5) * m.Fx) * m.ir;
     m.uy = (jy + R(0.5) * m.Fy) * m.ir;
     mac_qe(m);
@@ -152,7 +168,7 @@ LBM_HD void macros(const Params<R>& P, R rho_d, R jx, R jy, R sg, Mac<R>& m) {
     R E_d = (m.rhoE_d - rho_d * P.E0) * m.ir;
     m.T_d = (E_d - R(0.5) * (m.ux * m.ux + m.uy * m.uy)) * P.inv_Cv;
     m.T = P.T0 + m.T_d;
-    m.p_d = eos_dev(P, rho_d, m.rho, m.T_d, m.T);
+    m.p_d = eos_dev<MC>(P, rho_d, m.rho, m.T_d, m.T);
     mac_tail(P, m);
 }
 
@@ -162,12 +178,12 @@ LBM_HD void compress(const Mac<R>& m, MacC<R>& c) {
     c.rhoE_d = m.rhoE_d; c.T_d = m.T_d; c.p_d = m.p_d;
 }
 
-template <typename R>
+template <int MC = MODEL_ANY, typename R>
 LBM_HD void expand(const Params<R>& P, const MacC<R>& c, Mac<R>& m) {
     m.rho_d = c.rho_d;
     m.rho = P.rho0 + c.rho_d;
     m.ir = c.ir;
-    mac_force(P, m);
+    mac_force<MC>(P, m);
     m.ux = c.ux;
     m.uy = c.uy;
     mac_qe(m);
@@ -184,7 +200,7 @@ template <typename R>
 LBM_HD void wall_macros(const Params<R>& P, R rho_d, R ux, R uy, R rhoE_d, Mac<R>& m) {
     m.rho_d = rho_d;
     m.rho = P.rho0 + rho_d;
-    m.ir = R(1) / m.rho;
+    m.ir = fdiv(R(1), m.rho);
     if (P.force_mode) { m.Fx = m.rho * P.Fx; m.Fy = m.rho * P.Fy; }
     else { m.Fx = P.Fx; m.Fy = P.Fy; }
     m.ux = ux;
@@ -195,7 +211,7 @@ LBM_HD void wall_macros(const Params<R>& P, R rho_d, R ux, R uy, R rhoE_d, Mac<R
     m.T_d = (E_d - R(0.5) * (ux * ux + uy * uy)) * P.inv_Cv;
     m.T = P.T0 + m.T_d;
     m.p_d = eos_dev(P, rho_d, m.rho, m.T_d, m.T);
-    m.eta_d = (R(3) * m.p_d - (R(2) + P.alpha1) * rho_d) / P.beta1;
+    m.eta_d = fdiv(R(3) * m.p_d - (R(2) + P.alpha1) * rho_d, P.beta1);
     m.rhoH = P.rho0E0_p0 + m.rhoE_d + m.p_d;
 }
 
@@ -208,19 +224,20 @@ struct Rates {
     R se, sq, sp, sj, sE;
 };
 
-template <typename R>
+template <int MC = MODEL_ANY, typename R>
 LBM_HD R viscosity(const Params<R>& P, R T) {
-    if (P.visc == 1) return P.mu0 * T * P.inv_T0;
-    if (P.visc == 2) {
+    const int law = visc_law<MC>(P);
+    if (law == 1) return P.mu0 * T * P.inv_T0;
+    if (law == 2) {
         R th = T * P.inv_T0;
         return fdiv(P.mu0 * th * sqrt(th) * (R(1) + P.visc_S), th + P.visc_S);
     }
     return P.mu0;
 }
 
-template <typename R>
+template <int MC = MODEL_ANY, typename R>
 LBM_HD void rates(const Params<R>& P, R rho_ir, R T, Rates<R>& r) {
-    R mu = viscosity(P, T);
+    R mu = viscosity<MC>(P, T);
     R nu = mu * rho_ir;
     r.sp = fdiv(R(1), R(0.5) + R(3) * nu);
     r.sq = fdiv(R(36) * nu, R(18) * nu + R(1));
@@ -370,11 +387,11 @@ struct KeepDFs {
 // moments, and for the final update after `reload(f, g)`; a caller that can
 // fetch them again (from shared memory) passes a reload that does so, and
 // the values need not stay in registers through the collision.
-template <typename R, typename Add, typename Reload = KeepDFs>
+template <int MC = MODEL_ANY, typename R, typename Add, typename Reload = KeepDFs>
 LBM_HD void collide(const Params<R>& P, const Mac<R>& mc, R* f, R* g, R grx, R gry, R gpx, R gpy,
                     const Add& add, const Reload& reload = Reload()) {
     Rates<R> r;
-    rates(P, mc.ir, mc.T, r);
+    rates<MC>(P, mc.ir, mc.T, r);
     R m[9], n[9];
     moments(f, m);
     moments(g, n);
@@ -386,7 +403,7 @@ LBM_HD void collide(const Params<R>& P, const Mac<R>& mc, R* f, R* g, R grx, R g
 
     // corrections C = R G + T grad(rho) + X grad(p) on rows 1, 7, 8 (Sec. 2.1)
     R C1 = R(0), C7 = R(0), C8 = R(0);
-    if (P.corrections) {
+    if (corrections_on<MC>(P)) {
         R ux2 = ux * ux, uy2 = uy * uy, sum2 = ux2 + uy2, dif2 = ux2 - uy2, xy = ux * uy;
         R tse = R(2) - r.se, tsp = R(2) - r.sp;
         R q1 = fdiv(r.sp * tse, tsp), q7 = fdiv(r.se * tsp, tse);
@@ -517,8 +534,9 @@ LBM_HD void rebuild(const Params<R>& P, const Mac<R>& mb, const R* mt, const R* 
     rates(P, mb.ir, mb.T, r);
     const R ux = mb.ux, uy = mb.uy;
     R he = R(1) - R(0.5) * r.se, hq = R(1) - R(0.5) * r.sq, hp = R(1) - R(0.5) * r.sp;
-    R v1 = mt[1] / he, v2 = mt[2] / he, v4 = mt[4] / hq, v6 = mt[6] / hq;
-    R v7 = mt[7] / hp, v8 = mt[8] / hp;
+    const R ihe = fdiv(R(1), he), ihq = fdiv(R(1), hq), ihp = fdiv(R(1), hp);
+    R v1 = mt[1] * ihe, v2 = mt[2] * ihe, v4 = mt[4] * ihq, v6 = mt[6] * ihq;
+    R v7 = mt[7] * ihp, v8 = mt[8] * ihp;
     R mn1 = v1 - R(0.5) * P.kk * r.se * v2 - R(0.5) * P.hh * r.sq * (ux * v4 + uy * v6);
     R mn7 = v7 - P.bb * r.sq * (ux * v4 - uy * v6);
     R mn8 = v8 - R(0.5) * P.bb * r.sq * (uy * v4 + ux * v6);
@@ -539,9 +557,10 @@ LBM_HD void rebuild(const Params<R>& P, const Mac<R>& mb, const R* mt, const R* 
     R Y3 = ux * (mt[1] * R(1.0 / 3.0) + mt[7]) + R(2) * uy * mt[8];
     R Y5 = uy * (mt[1] * R(1.0 / 3.0) - mt[7]) + R(2) * ux * mt[8];
     R hE = R(1) - R(0.5) * r.sE, hj = R(1) - R(0.5) * r.sj;
-    R w1 = nt[1] / hE, w2 = nt[2] / hE, w7 = nt[7] / hE, w8 = nt[8] / hE;
-    R w3 = (nt[3] - R(0.5) * Y3) / hj, w4 = (nt[4] + R(0.5) * Y3) / hj;
-    R w5 = (nt[5] - R(0.5) * Y5) / hj, w6 = (nt[6] + R(0.5) * Y5) / hj;
+    const R ihE = fdiv(R(1), hE), ihj = fdiv(R(1), hj);
+    R w1 = nt[1] * ihE, w2 = nt[2] * ihE, w7 = nt[7] * ihE, w8 = nt[8] * ihE;
+    R w3 = (nt[3] - R(0.5) * Y3) * ihj, w4 = (nt[4] + R(0.5) * Y3) * ihj;
+    R w5 = (nt[5] - R(0.5) * Y5) * ihj, w6 = (nt[6] + R(0.5) * Y5) * ihj;
     R nn3 = w3 - R(0.5) * r.sj * w4;
     R nn5 = w5 - R(0.5) * r.sj * w6;
     EDev<R> e;

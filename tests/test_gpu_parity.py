@@ -243,15 +243,73 @@ def test_warp_strips_walls_fp64(orc, lbm, tile):
 def test_warp_strips_equal_block_strips(lbm, precision):
     # the warp-strip kernel runs the per-node arithmetic of the block-strip
     # kernel on the same inputs: the two give the same bits
-    cfg = W.cavity(N=97, Ra=2e3, eps=0.5, precision=precision)
+    cfg = W.cavity(N=197, Ra=2e3, eps=0.5, precision=precision)
     a, b = lbm.Lattice(cfg), lbm.Lattice(cfg)
-    a.set_tile(128, 16, 0)
-    b.set_tile(60, 11, 4)
+    a.set_tile(128, 16, 0)  # both shapes run the instance specialised for the cavity model
+    b.set_tile(30, 11, 4)
     a.step(300)
     b.step(300)
     fa, ga = a.get_state()
     fb, gb = b.get_state()
     assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+
+
+@pytest.mark.parametrize("eos", [(W.EOS_IDEAL, ()), (W.EOS_CUBIC, (0.05, 0.2))])
+def test_cavity_model_instance_fp64(orc, lbm, eos):
+    # the default shape runs the kernel instance specialised for the cavity
+    # model (Sutherland, F = rho g, corrections; ideal or cubic EOS)
+    cfg = W.cavity(N=190, Ra=2e3, eps=0.5, eos=eos, gamma=1.3 if eos[0] == W.EOS_CUBIC else 1.4)
+    _, _, err = pair(orc, lbm, cfg, 300)
+    assert_close(err, TOL64)
+
+
+@pytest.mark.parametrize("eos", [(W.EOS_IDEAL, ()), (W.EOS_CUBIC, (0.05, 0.2))])
+def test_cavity_model_instance_vs_generic_fp32(lbm, eos):
+    # pair 3 (macros recomputed at collision time) runs the generic instance
+    cfg = W.cavity(N=190, Ra=2e3, eps=0.5, eos=eos, gamma=1.3 if eos[0] == W.EOS_CUBIC else 1.4, precision=1)
+    g, h = lbm.Lattice(cfg), lbm.Lattice(cfg)
+    h.set_tile(64, 9, 3)
+    g.step(800)
+    h.step(800)
+    mg, mh = g.macros(), h.macros()
+    umax = np.hypot(mg["ux"], mg["uy"]).max()
+    assert rel(mh["rho"], mg["rho"]) < 1e-5 and rel(mh["T"], mg["T"]) < 1e-5
+    assert np.abs(mh["ux"] - mg["ux"]).max() / umax < 1e-4
+
+
+def test_model_classes_batched_equal_alone(lbm):
+    # a cavity of 64^2 nodes runs the generic instance, one of 200^2 the
+    # cavity instance; a batch launches them as two groups: every member
+    # steps as it would alone
+    import torch
+    stream = torch.cuda.Stream()
+    cfgs = [W.cavity(N=64, Ra=1e3, eps=0.3, precision=1), W.cavity(N=200, Ra=1e4, eps=0.3, precision=1),
+            W.couette(nx=40, ny=12, precision=1)]
+    alone = [lbm.Lattice(c, stream=stream) for c in cfgs]
+    mixed = [lbm.Lattice(c, stream=stream) for c in cfgs]
+    b = lbm.Batch(mixed, graph_steps=0)
+    b.step(30)
+    for a in alone:
+        a.step(30)
+    stream.synchronize()
+    for a, m in zip(alone, mixed):
+        fa, ga = a.get_state()
+        fm, gm = m.get_state()
+        assert np.array_equal(fa, fm) and np.array_equal(ga, gm)
+    b.close()
+
+
+def test_batch_rejects_changed_eos_class(lbm):
+    import torch
+    stream = torch.cuda.Stream()
+    cfg = W.cavity(N=200, Ra=1e3, eps=0.3)  # large enough for the cavity instance
+    lat = lbm.Lattice(cfg, stream=stream)
+    b = lbm.Batch([lat], graph_steps=0)
+    b.step(2)
+    lat.check(lat.L.lbm_set_eos(lat.h, W.EOS_DECOUPLING, None, 0))
+    with pytest.raises(Exception):
+        b.step(2)
+    b.close()
 
 
 def test_lean_one_node_shape_matches_oracle(orc, lbm):
