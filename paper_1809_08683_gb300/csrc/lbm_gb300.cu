@@ -1518,7 +1518,7 @@ __device__ void wall_node(const InstDesc* D, int k, WallNode& n) {
 }
 
 template <typename R>
-__global__ void __launch_bounds__(128) k_boundary(const BWork* __restrict__ work,
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 2) k_boundary(const BWork* __restrict__ work,
                                                   InstDesc* const* __restrict__ descs, int step_par,
                                                   long long* __restrict__ counter) {
     __shared__ Params<R> P;
@@ -1538,10 +1538,13 @@ __global__ void __launch_bounds__(128) k_boundary(const BWork* __restrict__ work
     WallNode n;
     wall_node(D, k, n);
 
-    // density (and Neumann total energy) from the bounced-back populations
-    R v[18];
+    // the wall node's and x_f's populations, loaded together so that their
+    // latencies overlap (the pass is bound by them)
+    R v[18], u[18];
     const long long ib = (long long)n.y * pitch + n.x;
     load18<R>(buf, plane, ib, v);
+    load18<R>(buf, plane, (long long)(n.y + n.dy) * pitch + (n.x + n.dx), u);
+    // density (and Neumann total energy) from the bounced-back populations
     R rd, jx, jy, sg;
     lbm::node_sums(v, v + 9, rd, jx, jy, sg);
     const R ux = R(n.ux), uy = R(n.uy);
@@ -1562,9 +1565,7 @@ __global__ void __launch_bounds__(128) k_boundary(const BWork* __restrict__ work
     // redefined non-equilibrium moments at x_f (and x_ff), extrapolated
     R mt[9], nt[9];
     {
-        R u[18];
         Mac<R> m;
-        load18<R>(buf, plane, (long long)(n.y + n.dy) * pitch + (n.x + n.dx), u);
         node_macros(P, u, m);
         lbm::tilde_neq(P, m, u, u + 9, mt, nt);
         if (n.order == 2) {
