@@ -88,12 +88,17 @@ KERNEL_SOURCES = ("lbm_gb300.cu", "lbm_node.cuh", "lbm_f2.cuh")
 
 
 def kernel_source_hash():
-    """SHA-256 over the kernel sources, to tell whether a stored ncu figure
-    still describes the kernels being run."""
+    """SHA-256 over the kernel sources with comments and blank space
+    removed, to tell whether a stored ncu figure still describes the
+    kernels being run (a comment edit does not change the code)."""
+    import re
     h = hashlib.sha256()
     for name in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_1809_08683_gb300", "csrc", name), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1809_08683_gb300", "csrc", name), encoding="utf-8") as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()
 
 

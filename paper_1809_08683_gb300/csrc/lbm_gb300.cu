@@ -12,11 +12,15 @@
 //   k_boundary       : every wall node of the other buffer is rebuilt from its
 //                      bounced sums, the wall data and the extrapolated
 //                      redefined non-equilibrium moments (Sec. 3).
-// The fused kernel assigns each CTA a strip of BX columns and a run of rows.
-// It sweeps the run row by row, keeping rho' and p' of the rows j-1, j, j+1
-// (plus one halo column on each side) in a shared-memory ring, so the
-// gradients of the correction terms T grad(rho) and X grad(p) need no extra
-// pass over HBM.
+// The fused kernels sweep a run of rows of a strip of columns row by row:
+// each row is staged into shared memory by one TMA tensor copy, and rho' and
+// p' of the rows j-1, j, j+1 (plus one halo column on each side) stay in a
+// shared-memory ring (block strips) or in registers and neighbouring lanes
+// (warp strips), so the gradients of the correction terms T grad(rho) and
+// X grad(p) need no extra pass over HBM.  Block strips of 128 columns
+// (k_collide_stream) are the default shape; warp strips (k_collide_warp),
+// paired warp strips (k_collide_warp2) and paired block strips
+// (k_collide_pair) are the alternatives lbm_set_tile selects.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -363,10 +367,11 @@ struct alignas(2 * sizeof(R)) RhoP {
     R r, p;
 };
 
-// Shared-memory layout of the fused kernel: S stages of one lattice row of
-// the CTA's strip (18 planes, each [16-byte left-halo chunk][BX][16-byte
-// right-halo chunk]), one mbarrier per stage, the parameters, and a 4-row
-// ring of rho' and p' over the strip plus its two halo columns.
+// Shared-memory layout of the block-strip kernel: S stages of one lattice
+// row of the CTA's strip (18 planes, each [16-byte left-halo chunk][BX]
+// [16-byte right-halo chunk], 128-byte aligned for the tensor copy), one
+// mbarrier per stage, the parameters, and a 4-row ring of (rho', p') pairs
+// over the strip plus its two halo columns.
 template <typename R, int BX, int S>
 struct FusedSmem {
     static constexpr int E = 16 / (int)sizeof(R);  // elements per 16-byte chunk
