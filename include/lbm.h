@@ -175,7 +175,8 @@ const char* lbm_last_error(void);
 /* Batched stepping: contexts (same stream, any size/EOS/precision mix) are
  * advanced together, one fused launch per group of members sharing a
  * precision, launch shape and model class (lattices of 32768 nodes or more
- * with the heated-cavity model, ideal or cubic EOS, run a specialised
+ * with the heated-cavity model (Sutherland viscosity, F = rho g with
+ * force[0] == 0, corrections on), ideal or cubic EOS, run a specialised
  * kernel instance, all others the generic one) and one wall-pass launch per
  * precision per step.  A lattice gives the same bits alone or batched.
  * graph_steps > 0 captures that many steps in a CUDA graph that

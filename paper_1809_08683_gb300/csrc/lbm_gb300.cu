@@ -2632,8 +2632,8 @@ lbm_status lbm_set_eos(lbm_ctx* c, int kind, const double* params, int np) {
     P.visc = k.visc_law;
     P.force_mode = k.force_mode;
     P.corrections = k.corrections;
-    c->mc = (k.visc_law == 2 && k.force_mode == 1 && k.corrections && (kind == lbm::EOS_IDEAL || kind == lbm::EOS_CUBIC) &&
-             (long long)k.nx * k.ny >= kModelMinNodes)
+    c->mc = (k.visc_law == 2 && k.force_mode == 1 && k.corrections && k.force[0] == 0.0 &&
+             (kind == lbm::EOS_IDEAL || kind == lbm::EOS_CUBIC) && (long long)k.nx * k.ny >= kModelMinNodes)
                 ? lbm::MODEL_CAVITY
                 : lbm::MODEL_ANY;
     c->h.pd = P;

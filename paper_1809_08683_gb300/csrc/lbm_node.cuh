@@ -73,9 +73,10 @@ enum { EOS_DECOUPLING = 0, EOS_IDEAL = 1, EOS_CS = 2, EOS_CUBIC = 3 };
 // Model classes.  MODEL_ANY reads the EOS, the viscosity law, the force
 // mode and the corrections flag from the parameters at run time.
 // MODEL_CAVITY fixes the heated-cavity model at compile time (Sutherland
-// viscosity, F = rho g, corrections on) and keeps only the ideal-gas and
-// cubic EOS, chosen at run time.  The arithmetic is the same; a fixed model
-// drops the branches and the code of the others.
+// viscosity, F = rho g with vertical g, corrections on) and keeps only the
+// ideal-gas and cubic EOS, chosen at run time.  The arithmetic is the same;
+// a fixed model drops the branches and the code of the others, and the
+// terms of F_x = 0.
 enum { MODEL_ANY = 0, MODEL_CAVITY = 1 };
 template <int MC, typename R>
 LBM_HD int visc_law(const Params<R>& P) { return MC != MODEL_ANY ? 2 : P.visc; }
@@ -141,11 +142,15 @@ LBM_HD R eos_dev(const Params<R>& P, R rho_d, R rho, R T_d, R T) {
 // Body force F = rho g (force_mode 1) or F = g, and q = u . F.
 template <int MC = MODEL_ANY, typename R>
 LBM_HD void mac_force(const Params<R>& P, Mac<R>& m) {
-    if (force_is_rho_g<MC>(P)) { m.Fx = m.rho * P.Fx; m.Fy = m.rho * P.Fy; }
+    if (MC == MODEL_CAVITY) { m.Fx = R(0); m.Fy = m.rho * P.Fy; }
+    else if (force_is_rho_g<MC>(P)) { m.Fx = m.rho * P.Fx; m.Fy = m.rho * P.Fy; }
     else { m.Fx = P.Fx; m.Fy = P.Fy; }
 }
-template <typename R>
-LBM_HD void mac_qe(Mac<R>& m) { m.qe = m.ux * m.Fx + m.uy * m.Fy; }
+template <int MC = MODEL_ANY, typename R>
+LBM_HD void mac_qe(Mac<R>& m) {
+    if (MC == MODEL_CAVITY) m.qe = m.uy * m.Fy;
+    else m.qe = m.ux * m.Fx + m.uy * m.Fy;
+}
 
 // eta' = (3 p' - (2 + alpha1) rho') / beta1 and rho H - rho0 H0 + p0.
 template <typename R>
@@ -161,9 +166,9 @@ LBM_HD void macros(const Params<R>& P, R rho_d, R jx, R jy, R sg, Mac<R>& m) {
     m.rho = P.rho0 + rho_d;
     m.ir = fdiv(R(1), m.rho);
     mac_force<MC>(P, m);
-    m.ux = (jx + R(0.5) * m.Fx) * m.ir;
+    m.ux = MC == MODEL_CAVITY ? jx * m.ir : (jx + R(0.5) * m.Fx) * m.ir;
     m.uy = (jy + R(0.5) * m.Fy) * m.ir;
-    mac_qe(m);
+    mac_qe<MC>(m);
     m.rhoE_d = sg + R(0.5) * m.qe;
     R E_d = (m.rhoE_d - rho_d * P.E0) * m.ir;
     m.T_d = (E_d - R(0.5) * (m.ux * m.ux + m.uy * m.uy)) * P.inv_Cv;
@@ -186,7 +191,7 @@ LBM_HD void expand(const Params<R>& P, const MacC<R>& c, Mac<R>& m) {
     mac_force<MC>(P, m);
     m.ux = c.ux;
     m.uy = c.uy;
-    mac_qe(m);
+    mac_qe<MC>(m);
     m.rhoE_d = c.rhoE_d;
     m.T_d = c.T_d;
     m.T = P.T0 + c.T_d;
@@ -256,7 +261,7 @@ struct Dev {
     R F1, F2, F4, F6, F7, F8;        // F_m rows (F_m3 = Fx, F_m5 = Fy)
 };
 
-template <typename R>
+template <int MC = MODEL_ANY, typename R>
 LBM_HD void neq_density(const Params<R>& P, const Mac<R>& m, R m1, R m2, R m4, R m6, R m7, R m8,
                         Dev<R>& d) {
     R ux = m.ux, uy = m.uy, rho = m.rho;
@@ -270,13 +275,24 @@ LBM_HD void neq_density(const Params<R>& P, const Mac<R>& m, R m1, R m2, R m4, R
     d.me8 = rho * ux * uy;
     // F_m, Sec. 2.1, bracket by the product rule
     R Fx = m.Fx, Fy = m.Fy;
-    R Fu = Fx * ux + Fy * uy;
-    d.F1 = R(6) * Fu;
-    d.F2 = -R(6) * Fu + R(18) * (Fx * ux * uy2 + Fy * uy * ux2);
-    d.F4 = -Fx + R(3) * (Fx * uy2 + R(2) * Fy * ux * uy);
-    d.F6 = -Fy + R(3) * (Fy * ux2 + R(2) * Fx * ux * uy);
-    d.F7 = R(2) * (Fx * ux - Fy * uy);
-    d.F8 = Fx * uy + Fy * ux;
+    if (MC == MODEL_CAVITY) {
+        // the same terms with F_x = 0
+        R Fu = Fy * uy;
+        d.F1 = R(6) * Fu;
+        d.F2 = -R(6) * Fu + R(18) * (Fy * uy * ux2);
+        d.F4 = R(3) * (R(2) * Fy * ux * uy);
+        d.F6 = -Fy + R(3) * (Fy * ux2);
+        d.F7 = R(2) * (-Fy * uy);
+        d.F8 = Fy * ux;
+    } else {
+        R Fu = Fx * ux + Fy * uy;
+        d.F1 = R(6) * Fu;
+        d.F2 = -R(6) * Fu + R(18) * (Fx * ux * uy2 + Fy * uy * ux2);
+        d.F4 = -Fx + R(3) * (Fx * uy2 + R(2) * Fy * ux * uy);
+        d.F6 = -Fy + R(3) * (Fy * ux2 + R(2) * Fx * ux * uy);
+        d.F7 = R(2) * (Fx * ux - Fy * uy);
+        d.F8 = Fx * uy + Fy * ux;
+    }
     d.d1 = m1 - d.me1 + R(0.5) * d.F1;
     d.d2 = m2 - d.me2 + R(0.5) * d.F2;
     d.d4 = m4 - d.me4 + R(0.5) * d.F4;
@@ -396,7 +412,7 @@ LBM_HD void collide(const Params<R>& P, const Mac<R>& mc, R* f, R* g, R grx, R g
     moments(f, m);
     moments(g, n);
     Dev<R> d;
-    neq_density(P, mc, m[1], m[2], m[4], m[6], m[7], m[8], d);
+    neq_density<MC>(P, mc, m[1], m[2], m[4], m[6], m[7], m[8], d);
     Gv<R> G;
     const R ux = mc.ux, uy = mc.uy;
     apply_IS2(P, r, ux, uy, d, G);
