@@ -157,13 +157,15 @@ lbm_status lbm_derived(const lbm_ctx* ctx, double* out8);
  * Used by the autotuner. */
 lbm_status lbm_set_tile(lbm_ctx* ctx, int bx, int by, int pair);
 
-/* Launch shape in use: the default chosen by lbm_create or the one set by
- * lbm_set_tile.  Default: block strips, pair = 0, bx = 128, or warp strips,
- * pair = 4, bx = 30, for nx <= 160 (same results); by = ny / 128 between 1
- * and 24 (FP32) or 8 (FP64).  by is
+/* Launch shape in use: the default chosen by lbm_create and lbm_set_eos, or
+ * the one set by lbm_set_tile.  Default: warp strips, pair = 4, bx = 30, for
+ * nx <= 160; paired block strips, pair = 1, bx = 128, for wider FP32
+ * lattices of the heated-cavity model class (see lbm_batch_create); block
+ * strips, pair = 0, bx = 128, otherwise.  by = ny / 128 between 1 and 24
+ * (FP32) or 8 (FP64); 3 ny / 512 between 1 and 12 for pair = 1.  by is
  * the run length when the lattice is stepped alone; a batch uses runs of
- * up to 24 (FP32) or 8 (FP64) rows for members whose shape was not set,
- * shortened until the batch fills the GPU. */
+ * up to 24 (FP32; 32 for pair = 1) or 8 (FP64) rows for members whose
+ * shape was not set, shortened until the batch fills the GPU. */
 lbm_status lbm_get_tile(const lbm_ctx* ctx, int* bx, int* by, int* pair);
 
 /* Steps taken since the last (re)initialisation. */

@@ -4,7 +4,7 @@
 // Data layout in HBM, per lattice: two buffers (A, B), each 18 planes
 // (f'_0..f'_8, g'_0..g'_8) of ny rows with a pitch of nx rounded up to 32
 // elements, FP64 or FP32.  One time step is
-//   k_collide_stream : every node is loaded once from the current buffer,
+//   fused kernel     : every node is loaded once from the current buffer,
 //                      collided (Eqs. LBE.u.c, LBE.T.c) and pushed into the
 //                      other buffer (Eqs. LBE.u.s, LBE.T.s); a population that
 //                      would leave the domain is written back reversed into the
@@ -17,10 +17,11 @@
 // p' of the rows j-1, j, j+1 (plus one halo column on each side) stay in a
 // shared-memory ring (block strips) or in registers and neighbouring lanes
 // (warp strips), so the gradients of the correction terms T grad(rho) and
-// X grad(p) need no extra pass over HBM.  Block strips of 128 columns
-// (k_collide_stream) are the default shape; warp strips (k_collide_warp),
-// paired warp strips (k_collide_warp2) and paired block strips
-// (k_collide_pair) are the alternatives lbm_set_tile selects.
+// X grad(p) need no extra pass over HBM.  The fused kernels are block strips
+// (k_collide_stream), warp strips (k_collide_warp), paired block strips
+// (k_collide_pair: two nodes per thread in packed FP32) and paired warp
+// strips (k_collide_warp2); default_shape picks one per lattice and
+// lbm_set_tile selects any other.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -929,7 +930,7 @@ struct AddDither2 {
 #define LBM_PAIR_WARPS_PER_SM 12  // resident warps per SM with the row macros kept in registers
 #endif
 
-template <int BX, bool KEEP>
+template <int BX, bool KEEP, int MC = lbm::MODEL_ANY>
 __global__ void __launch_bounds__(BX / 2, (KEEP ? LBM_PAIR_WARPS_PER_SM : 12) * 64 / BX) k_collide_pair(const Work* __restrict__ work,
                                                                     InstDesc* const* __restrict__ descs,
                                                                     int step_par, const long long* __restrict__ counter) {
@@ -981,9 +982,12 @@ __global__ void __launch_bounds__(BX / 2, (KEEP ? LBM_PAIR_WARPS_PER_SM : 12) * 
     const int last_l = nrows + 1;
     const int ca = 2 * tid + 2;                 // ring column of x_a
     const int cr = (xlast - w.x0) + 3;          // ring column of the right halo
+    // vertically adjacent runs sweep in opposite directions (as in
+    // k_collide_stream): logical rows 0..last_l are physical y0-1..y1 or y1..y0-1
+    const bool down = w.dir != 0;
 
     auto phys = [&](int l) -> int {
-        int y = w.y0 - 1 + l;
+        int y = down ? w.y1 - l : w.y0 - 1 + l;
         if (y < 0 || y >= ny) {
             if (!py) return -1;
             y = (y < 0) ? y + ny : y - ny;
@@ -1040,7 +1044,7 @@ __global__ void __launch_bounds__(BX / 2, (KEEP ? LBM_PAIR_WARPS_PER_SM : 12) * 
             f2 rd, jx, jy, sg;
             lbm::node_sums(v, v + 9, rd, jx, jy, sg);
             Mac<f2> m;
-            lbm::macros(P2, rd, jx, jy, sg, m);
+            lbm::macros<MC>(P2, rd, jx, jy, sg, m);
             compress(m, mk);
             if (act_b) {
                 *reinterpret_cast<float2*>(&s_rho[slot][ca]) = m.rho_d.v;
@@ -1063,7 +1067,7 @@ __global__ void __launch_bounds__(BX / 2, (KEEP ? LBM_PAIR_WARPS_PER_SM : 12) * 
             Mac<float> h;
 #pragma unroll
             for (int q = 0; q < 18; ++q) v[q] = st[q * W + off];
-            node_macros(P1, v, h);
+            node_macros<MC>(P1, v, h);
             s_rho[slot][col] = h.rho_d;
             s_p[slot][col] = h.p_d;
         }
@@ -1076,7 +1080,7 @@ __global__ void __launch_bounds__(BX / 2, (KEEP ? LBM_PAIR_WARPS_PER_SM : 12) * 
     row_macros(1, mc);
 
     for (int k = 0; k < nrows; ++k) {
-        const int j = w.y0 + k;
+        const int j = down ? w.y1 - 1 - k : w.y0 + k;
         if (phys(k + 2) >= 0) row_macros(k + 2, mn);
         __syncthreads();
         if (s_abort) break;
@@ -1085,7 +1089,8 @@ __global__ void __launch_bounds__(BX / 2, (KEEP ? LBM_PAIR_WARPS_PER_SM : 12) * 
         if (act_a) {
             if (KEEP && !(isfinite(mc.rho_d.v.x) && isfinite(mc.T_d.v.x) && isfinite(mc.rho_d.v.y) && isfinite(mc.T_d.v.y)))
                 atomicOr(status, act_b ? 1u : ((isfinite(mc.rho_d.v.x) && isfinite(mc.T_d.v.x)) ? 0u : 1u));
-            const int sm = k & 3, s0 = (k + 1) & 3, sp = (k + 2) & 3;
+            // ring slots of the rows j - 1 (sm), j, j + 1 (sp)
+            const int sm = (down ? k + 2 : k) & 3, s0 = (k + 1) & 3, sp = (down ? k : k + 2) & 3;
             // interior stencil for both nodes: columns (ca-1, ca) on the left, (ca+1, ca+2) on the right
             auto grad = [&](float (*a)[RW], f2& gx, f2& gy) {
                 const float2 cm = *reinterpret_cast<const float2*>(&a[sm][ca]);
@@ -1114,25 +1119,35 @@ __global__ void __launch_bounds__(BX / 2, (KEEP ? LBM_PAIR_WARPS_PER_SM : 12) * 
                     const bool onS = !py && j == 0, onN = !py && j == ny - 1;
                     const bool onW = !px && x == 0, onE = !px && x == nx - 1;
                     if (!(onS || onN || onW || onE)) continue;
+                    // rho', p' two nodes inward: along x from the ring when the
+                    // strip or one of its halo columns holds that column, else
+                    // (and along y) from the source buffer
+                    const int dx = onW ? 1 : -1, dy = onS ? 1 : -1;
+                    float rx2 = 0.0f, px2 = 0.0f, ry2 = 0.0f, py2 = 0.0f;
+                    if (onW || onE) {
+                        const int c2 = c + 2 * dx;
+                        if ((c2 >= 2 && c2 < cr) || (c2 == 1 && has_l) || (c2 == cr && has_r)) {
+                            rx2 = s_rho[s0][c2];
+                            px2 = s_p[s0][c2];
+                        } else {
+                            rho_p_at<MC>(P1, src, plane, pitch, x + 2 * dx, j, rx2, px2);
+                        }
+                    }
+                    if (onS || onN) rho_p_at<MC>(P1, src, plane, pitch, x, j + 2 * dy, ry2, py2);
                     float gr[4];
+#pragma unroll
                     for (int fld = 0; fld < 2; ++fld) {
                         float (*a)[RW] = fld ? s_p : s_rho;
                         const float v0 = a[s0][c];
                         float gxs, gys;
                         if (onW || onE) {
-                            const int dx = onW ? 1 : -1;
-                            float r2, p2;
-                            rho_p_at(P1, src, plane, pitch, x + 2 * dx, j, r2, p2);
-                            gxs = (float)dx * (-3.0f * v0 + 4.0f * a[s0][c + dx] - (fld ? p2 : r2)) * 0.5f;
+                            gxs = (float)dx * (-3.0f * v0 + 4.0f * a[s0][c + dx] - (fld ? px2 : rx2)) * 0.5f;
                         } else {
                             gxs = (a[s0][c + 1] - a[s0][c - 1]) * 0.5f;
                         }
                         if (onS || onN) {
-                            const int dy = onS ? 1 : -1;
-                            float r2, p2;
-                            rho_p_at(P1, src, plane, pitch, x, j + 2 * dy, r2, p2);
                             const float v1 = onS ? a[sp][c] : a[sm][c];
-                            gys = (float)dy * (-3.0f * v0 + 4.0f * v1 - (fld ? p2 : r2)) * 0.5f;
+                            gys = (float)dy * (-3.0f * v0 + 4.0f * v1 - (fld ? py2 : ry2)) * 0.5f;
                         } else {
                             gys = (a[sp][c] - a[sm][c]) * 0.5f;
                         }
@@ -1150,11 +1165,11 @@ __global__ void __launch_bounds__(BX / 2, (KEEP ? LBM_PAIR_WARPS_PER_SM : 12) * 
             for (int q = 0; q < 18; ++q) v[q] = f2(*reinterpret_cast<const float2*>(st + q * W));
             Mac<f2> mf;
             if (KEEP) {
-                expand(P2, mc, mf);
+                lbm::expand<MC>(P2, mc, mf);
             } else {
                 f2 rd, jx, jy, sg;
                 lbm::node_sums(v, v + 9, rd, jx, jy, sg);
-                lbm::macros(P2, rd, jx, jy, sg, mf);
+                lbm::macros<MC>(P2, rd, jx, jy, sg, mf);
                 if (!(isfinite(mf.rho_d.v.x) && isfinite(mf.T_d.v.x) && (!act_b || (isfinite(mf.rho_d.v.y) && isfinite(mf.T_d.v.y)))))
                     atomicOr(status, 1u);
             }
@@ -1167,7 +1182,7 @@ __global__ void __launch_bounds__(BX / 2, (KEEP ? LBM_PAIR_WARPS_PER_SM : 12) * 
                     g[q] = f2(*reinterpret_cast<const float2*>(st + (9 + q) * W));
                 }
             };
-            lbm::collide(P2, mf, v, v + 9, grx, gry, gpx, gpy, add, reload);
+            lbm::collide<MC>(P2, mf, v, v + 9, grx, gry, gpx, gpy, add, reload);
 
             push_pair(dst, v, xa, act_b, j, nx, ny, pitch, plane, px, py);
         }
@@ -2066,26 +2081,29 @@ void ensure_tick(std::vector<BWork>& v, int inst, int par) {
     }
 }
 
-// Default launch shape: block strips of 128 columns (pair 0), which with
-// each row staged by one tensor copy measured fastest on every square FP32
-// lattice from 512^2 to 4096^2 (4096^2: 0.58 ms against 0.62 ms for paired
-// and 0.63 ms for plain warp strips) and on the 96-cavity batch (one launch
-// for all members beats narrower strips for the ragged ones); FP64 is bound
-// by the FP64 pipe and prefers them too.  Lattices up to 160 columns wide
-// take warp strips of 30 columns (pair 4, same bits as pair 0): they waste
-// fewer lanes there and give small lattices more CTAs.
-void default_shape(const lbm_config& c, int& bx, int& pair) {
+// Default launch shape.  Lattices up to 160 columns wide take warp strips
+// of 30 columns (pair 4, same bits as pair 0): they waste fewer lanes there
+// and give small lattices more CTAs.  Wider FP32 lattices of the heated-
+// cavity model class take paired block strips of 128 columns (pair 1): two
+// nodes per thread in packed FP32 halve the arithmetic's issue slots (4096^2:
+// 0.49 ms against 0.55 ms for block strips; 96-cavity batch: 1.30 ms against
+// 1.39 ms per step).  All others take block strips of 128 columns (pair 0),
+// which also suit FP64, bound by the FP64 pipe.  The model class is known
+// once the EOS is set, so lbm_set_eos applies the shape.
+void default_shape(const lbm_config& c, int mc, int& bx, int& pair) {
     if (c.nx <= 160) { bx = 30; pair = 4; }
+    else if (c.precision == LBM_FP32_DEV && mc == lbm::MODEL_CAVITY) { bx = 128; pair = 1; }
     else { bx = 128; pair = 0; }
 }
 
 // Longest run of rows per CTA: the best measured on a 4096^2 (FP32) or
 // 2048^2 (FP64) lattice and on the 96-cavity batch (longer runs lose DRAM
 // and L2 locality between CTAs resident at the same time, shorter ones
-// re-stage more halo rows).
+// re-stage more halo rows).  Paired block strips: 32 rows on the 96-cavity
+// batch (1.285 ms per step against 1.302 ms with 24).
 int batch_rows(const lbm_config& c, int pair) {
     const bool f32 = c.precision == LBM_FP32_DEV;
-    const int by = pair == 0 ? (f32 ? 24 : 8) : (pair == 5 ? 16 : 24);
+    const int by = pair == 0 ? (f32 ? 24 : 8) : pair == 1 ? 32 : (pair == 5 ? 16 : 24);
     return std::min(c.ny, by);
 }
 
@@ -2093,12 +2111,15 @@ long long cta_count(const lbm_config& c, int bx, int by) {
     return (long long)((c.nx + bx - 1) / bx) * ((c.ny + by - 1) / by);
 }
 
-// Rows per run for a lattice launched on its own: ny / 128, between 1 and
-// the longest run.  Measured optimum on square FP32 lattices: 1-2 rows at
-// 256^2, 4 at 512^2, 8 at 1024^2, 12-16 at 2048^2, 24 at 4096^2; a small
+// Rows per run for a lattice launched on its own.  Block and warp strips:
+// ny / 128, between 1 and the longest run (measured optimum on square FP32
+// lattices: 1-2 rows at 256^2, 4 at 512^2, 8 at 1024^2, 12-16 at 2048^2, 24
+// at 4096^2).  Paired block strips: 3 ny / 512, between 1 and 12 (measured:
+// 2-4 at 512^2, 6 at 1024^2, 8-12 at 2048^2, 12 at 4096^2).  A small
 // lattice is latency-bound and gains more from spreading over more SMs than
 // it loses re-staging halo rows.
 int default_rows(const lbm_config& c, int pair) {
+    if (pair == 1) return std::max(1, std::min(std::min(batch_rows(c, pair), 12), c.ny * 3 / 512));
     return std::max(1, std::min(batch_rows(c, pair), c.ny / 128));
 }
 
@@ -2204,12 +2225,12 @@ cudaError_t configure_warp2() {
                                 (int)cudaSharedmemCarveoutMaxShared);
 }
 
-template <int BX, bool KEEP>
+template <int BX, bool KEEP, int MC = lbm::MODEL_ANY>
 cudaError_t configure_pair() {
-    cudaError_t e = cudaFuncSetAttribute(k_collide_pair<BX, KEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_collide_pair<BX, KEEP, MC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)PairSmem<BX>::bytes);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_collide_pair<BX, KEEP>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    return cudaFuncSetAttribute(k_collide_pair<BX, KEEP, MC>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                 (int)cudaSharedmemCarveoutMaxShared);
 }
 
@@ -2242,6 +2263,9 @@ lbm_status configure_kernels() {
     // the one-node-per-thread shapes, specialised for the heated-cavity models
     if (e == cudaSuccess) e = configure_models<float>();
     if (e == cudaSuccess) e = configure_models<double>();
+    if (e == cudaSuccess) e = configure_pair<64, true, lbm::MODEL_CAVITY>();
+    if (e == cudaSuccess) e = configure_pair<128, true, lbm::MODEL_CAVITY>();
+    if (e == cudaSuccess) e = configure_pair<256, true, lbm::MODEL_CAVITY>();
     if (e == cudaSuccess) e = configure_warp2<1>();
     if (e == cudaSuccess) e = configure_warp2<2>();
     if (e == cudaSuccess) e = configure_warp2<4>();
@@ -2329,10 +2353,10 @@ void launch_warp2_nw(const Work* work, int n, InstDesc* const* descs, int par, c
     k_collide_warp2<NW, S><<<n, 32 * NW, Warp2Smem<NW, S>::bytes, s>>>(work, descs, par, counter);
 }
 
-template <int BX, bool KEEP>
+template <int BX, bool KEEP, int MC = lbm::MODEL_ANY>
 void launch_pair_bx(const Work* work, int n, InstDesc* const* descs, int par, const long long* counter,
                     cudaStream_t s) {
-    k_collide_pair<BX, KEEP><<<n, BX / 2, PairSmem<BX>::bytes, s>>>(work, descs, par, counter);
+    k_collide_pair<BX, KEEP, MC><<<n, BX / 2, PairSmem<BX>::bytes, s>>>(work, descs, par, counter);
 }
 
 static const int kVariantWidth[kVariants] = {32, 64, 128, 64, 128, 256, 64, 128, 256, 32, 64, 128, 30, 60, 120,
@@ -2351,7 +2375,7 @@ int variant_index(int bx, int pair) {
 // so that all of them still give the same bits for a lattice; every other
 // shape runs the generic instance.
 int launch_model(int variant, int mc) {
-    return (variant <= 2 || (variant >= 12 && variant <= 14)) ? mc : lbm::MODEL_ANY;
+    return (variant <= 5 || (variant >= 12 && variant <= 14)) ? mc : lbm::MODEL_ANY;
 }
 
 template <typename R, int MC>
@@ -2361,6 +2385,9 @@ void launch_model_variant(const Work* work, int n, int variant, InstDesc* const*
     case 0: launch_collide_bx<R, 32, true, MC>(work, n, descs, par, counter, s); break;
     case 1: launch_collide_bx<R, 64, true, MC>(work, n, descs, par, counter, s); break;
     case 2: launch_collide_bx<R, 128, true, MC>(work, n, descs, par, counter, s); break;
+    case 3: launch_pair_bx<64, true, MC>(work, n, descs, par, counter, s); break;
+    case 4: launch_pair_bx<128, true, MC>(work, n, descs, par, counter, s); break;
+    case 5: launch_pair_bx<256, true, MC>(work, n, descs, par, counter, s); break;
     case 12: launch_warp_nw<R, 1, MC>(work, n, descs, par, counter, s); break;
     case 13: launch_warp_nw<R, 2, MC>(work, n, descs, par, counter, s); break;
     default: launch_warp_nw<R, 4, MC>(work, n, descs, par, counter, s); break;
@@ -2518,7 +2545,7 @@ lbm_status lbm_create(const lbm_config* cfg, void* workspace, size_t workspace_b
     InstDesc* p = c->d_desc;
     if (cudaMemcpyAsync(c->d_descs, &p, sizeof(p), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
         return cleanup(fail(LBM_ECUDA, "descs upload"));
-    default_shape(*cfg, c->bx, c->pair);
+    default_shape(*cfg, lbm::MODEL_ANY, c->bx, c->pair);
     c->by = default_rows(*cfg, c->pair);
     if ((st = upload_work(c)) != LBM_OK) return cleanup(st);
     c->h_bwork = make_bwork(*cfg, 0, 0);
@@ -2638,6 +2665,18 @@ lbm_status lbm_set_eos(lbm_ctx* c, int kind, const double* params, int np) {
                 : lbm::MODEL_ANY;
     c->h.pd = P;
     convert_params(P, c->h.pf);
+    if (!c->tile_set) {
+        // the default shape depends on the model class
+        int bx = 0, pair = 0;
+        default_shape(k, c->mc, bx, pair);
+        if (bx != c->bx || pair != c->pair) {
+            c->bx = bx;
+            c->pair = pair;
+            c->by = default_rows(k, pair);
+            lbm_status st = upload_work(c);
+            if (st != LBM_OK) return st;
+        }
+    }
 
     const double eta0 = (p0 / cs2 - (2.0 + P.alpha1) * r0) / P.beta1;
     const double mr[9] = {r0, 2.0 * P.alpha1 * r0 + 2.0 * P.beta1 * eta0, P.alpha2 * r0 + P.beta2 * eta0, 0, 0, 0, 0, 0, 0};

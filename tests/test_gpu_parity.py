@@ -157,9 +157,12 @@ def test_paired_fp32_periodic_ragged(orc, lbm, bx, by, pr):
     assert_close(err, TOL32)
 
 
-@pytest.mark.parametrize("tile", [(128, 16, 1), (64, 7, 1), (256, 16, 2)])
-def test_paired_fp32_walls(orc, lbm, tile):
-    cfg = W.cavity(N=67, Ra=1e3, eps=0.6, precision=1)
+@pytest.mark.parametrize("N,tile", [(67, (128, 16, 1)), (67, (64, 7, 1)), (67, (256, 16, 2)),
+                                    # east wall in a last strip of 1 or 2 columns: the node two
+                                    # columns inward lies beyond the strip's left halo, or in it
+                                    (65, (64, 7, 1)), (66, (64, 7, 1))])
+def test_paired_fp32_walls(orc, lbm, N, tile):
+    cfg = W.cavity(N=N, Ra=1e3, eps=0.6, precision=1)
     cfg["walls"][1]["u"] = (0.02, 0.0)
     o, g, err = pair(orc, lbm, cfg, 1500, tile=tile)
     assert_close(err, TOL32)
@@ -275,6 +278,16 @@ def test_cavity_model_instance_vs_generic_fp32(lbm, eos):
     umax = np.hypot(mg["ux"], mg["uy"]).max()
     assert rel(mh["rho"], mg["rho"]) < 1e-5 and rel(mh["T"], mg["T"]) < 1e-5
     assert np.abs(mh["ux"] - mg["ux"]).max() / umax < 1e-4
+
+
+@pytest.mark.parametrize("N,tile", [(190, (128, 12, 1)), (194, (64, 7, 1))])
+@pytest.mark.parametrize("eos", [(W.EOS_IDEAL, ()), (W.EOS_CUBIC, (0.05, 0.2))])
+def test_cavity_model_instance_paired_fp32(orc, lbm, N, tile, eos):
+    # paired block strips run the cavity instance too (N^2 >= 32768 nodes);
+    # 194 columns in strips of 64 leave a last strip of 2 columns
+    cfg = W.cavity(N=N, Ra=2e3, eps=0.5, eos=eos, gamma=1.3 if eos[0] == W.EOS_CUBIC else 1.4, precision=1)
+    o, g, err = pair(orc, lbm, cfg, 300, seed=N, df=1e-4, tile=tile)
+    assert_close(err, TOL32)
 
 
 def test_model_classes_batched_equal_alone(lbm):
