@@ -1537,8 +1537,16 @@ __device__ void wall_node(const InstDesc* D, int k, WallNode& n) {
     }
 }
 
+// Resident CTAs per SM of the FP32 wall pass.  3 leaves 146 registers per
+// thread and no spills; 4 spilled 68 bytes per thread and took 0.1055 ms per
+// step of the 96-cavity batch against 0.098 ms (6 and 8 CTAs, with more
+// spills: 0.137 and 0.159 ms).  The pass is latency-bound, and the spill
+// traffic costs more than the extra warps hide.
+#ifndef LBM_BOUNDARY_MINB
+#define LBM_BOUNDARY_MINB 3
+#endif
 template <typename R>
-__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 2) k_boundary(const BWork* __restrict__ work,
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? LBM_BOUNDARY_MINB : 2) k_boundary(const BWork* __restrict__ work,
                                                   InstDesc* const* __restrict__ descs, int step_par,
                                                   long long* __restrict__ counter) {
     __shared__ Params<R> P;
