@@ -2377,11 +2377,11 @@ int variant_index(int bx, int pair) {
     return -1;
 }
 
-// Model class a launch of `variant` can use: the one-node-per-thread shapes
-// that keep the row macros (block strips, variants 0-2; warp strips,
-// variants 12-14) have instances specialised for the heated-cavity model,
-// so that all of them still give the same bits for a lattice; every other
-// shape runs the generic instance.
+// Model class a launch of `variant` can use: the shapes that keep the row
+// macros (block strips, variants 0-2; paired block strips, variants 3-5;
+// warp strips, variants 12-14) have instances specialised for the
+// heated-cavity model (the one-node-per-thread ones still give the same bits
+// for a lattice); every other shape runs the generic instance.
 int launch_model(int variant, int mc) {
     return (variant <= 5 || (variant >= 12 && variant <= 14)) ? mc : lbm::MODEL_ANY;
 }
