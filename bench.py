@@ -13,7 +13,8 @@ Lines printed (one JSON line per run, rank 0):
             resident in HBM; state 11 GB >> 129 MB L2, so no flush is needed)
   e2e       same metric through the public API with host buffers: per bench
             step, equilibrium initialisation from pinned host fields (H2D),
-            the chunk of time steps, and the macroscopic fields back (D2H)
+            the chunk of time steps, and the macroscopic fields back (D2H);
+            one untimed round first, then --e2e-steps timed rounds
   roofline  the fused kernel's algorithmic bytes (18 DF reads + 18 DF writes
             per node) over its CUDA-event duration, against the measured HBM
             copy bandwidth
@@ -359,14 +360,18 @@ def main():
             host_in.append(fields)
         host_out = [[torch.empty((c["ny"], c["nx"]), dtype=torch.float64).pin_memory().numpy()
                      for _ in range(5)] for c in cfgs]
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
+        def e2e_step():
             for lat, f in zip(lats, host_in):
                 lat.init_macros(*f)
             batch.step(chunk)
             for lat, o in zip(lats, host_out):
                 lat.check(lat.L.lbm_macros(lat.h, *(lbm._ptr(a) for a in o)))
+
+        e2e_step()  # untimed warm-up: the first host round trip of a process runs slow
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
         barrier()
         el = time.perf_counter() - t0
         e2e = {"value": nodes * chunk * args.e2e_steps * world / el / 1e6, "unit": "MLUPS",
