@@ -53,6 +53,20 @@ def couette(nx=4, ny=64, U=0.05, T=1.0, tau0=0.8, Pr=0.71, gamma=1.4, precision=
                 eos={"kind": EOS_IDEAL, "params": []})
 
 
+def couette_variable_mu(nx=1, ny=32, Ma_e=0.1, tau0=0.8, Pr=0.71, gamma=1.4, eos=(EOS_IDEAL, ()), precision=0):
+    """Thermal Couette flow with mu / mu0 = T / T0 (Sec. 4.2): adiabatic lower
+    wall at rest (south, Neumann), upper wall moving at u = (U0, 0) and held
+    at T0 = 1 (north, Dirichlet), periodic in x, second-order extrapolation,
+    tau0 = 0.8 for mu0.  U0 = Ma_e sqrt(Cp T0) with Cp = gamma / (gamma - 1)
+    c_s^2 / T0, the heat capacity of the ideal and decoupling EOS at
+    rho0 = T0 = 1."""
+    cp = gamma / (gamma - 1.0) / 3.0
+    U0 = Ma_e * math.sqrt(cp)
+    return base(nx, ny, tau0=tau0, Pr=Pr, gamma=gamma, precision=precision, visc_law=VISC_LINEAR,
+                walls=[wall((0, 0), 1.0, 1, 2), wall((U0, 0), 1.0, 0, 2), periodic(), periodic()],
+                eos={"kind": int(eos[0]), "params": list(eos[1])})
+
+
 def poiseuille_force(ny, U0, tau0, rho0=1.0):
     """Body force F_x giving centreline velocity U0 in a channel of width
     W = ny - 1 for dynamic viscosity mu = rho0 (tau0 - 1/2) / 3:

@@ -11,6 +11,8 @@ import pytest
 
 from paper_1809_08683_gb300 import workloads as W
 
+from closed_forms import couette_mu_profile
+
 EX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1], dtype=float)
 EY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1], dtype=float)
 
@@ -184,6 +186,85 @@ def test_couette_closed_form(orc):
     # ideal gas at uniform pressure: rho T = const, with the initial mass
     rho_a = 64.0 / (1.0 / Ta).sum() / Ta
     assert _rel(m["rho"][:, 0], rho_a, 1.0) < 5e-3 or np.abs(m["rho"][:, 0] - rho_a).max() < 1e-6
+
+
+def test_couette_mu_profile_is_the_exact_solution():
+    # the closed form solves the steady equations it comes from: with
+    # mu = mu0 T / T0 the shear stress mu du/dy is uniform, and the energy
+    # balance (Cp / Pr) mu dT/dy + (mu du/dy) u = 0 (adiabatic at u = 0) holds
+    xi = np.linspace(0.0, 1.0, 20001)
+    Ma, Pr = 0.1, 20.0
+    s, T = couette_mu_profile(xi, Ma, Pr)
+    assert abs(s[0]) < 1e-15 and abs(s[-1] - 1.0) < 1e-13 and abs(T[-1] - 1.0) < 1e-13
+    ds, dT = np.gradient(s, xi), np.gradient(T, xi)
+    tau = T * ds
+    assert np.ptp(tau[1:-1]) / tau.mean() < 1e-7
+    # with U0 = T0 = 1 units: Ma^2 = U0^2 / (Cp T0), so Cp = 1 / Ma^2
+    resid = (1.0 / Ma ** 2 / Pr) * T * dT + tau * s
+    assert np.abs(resid[1:-1]).max() < 1e-7 * tau.mean()
+
+
+def test_couette_variable_viscosity_closed_form(orc):
+    # Sec. 4.2: mu / mu0 = T / T0, adiabatic lower wall at rest, lid at U0 and
+    # T0, ideal gas, tau0 = 0.8, 32 nodes across, Ma_e = 0.1 and Pr = 20
+    # (a = Pr Ma_e^2 / 2 = 0.1: 10% heating at the adiabatic wall, and a
+    # velocity profile 1.6% away from the linear one of constant viscosity).
+    ny, Pr = 32, 20.0
+    cfg = W.couette_variable_mu(nx=1, ny=ny, Ma_e=0.1, Pr=Pr)
+    o = orc.Oracle(cfg, threads=8)
+    d = o.derived()
+    U0 = cfg["walls"][1]["u"][0]
+    Ma = U0 / np.sqrt(d["Cp"] * 1.0)
+    assert abs(Ma - 0.1) < 1e-12
+    assert o.step(600000) == 0
+    m = o.macros()
+    xi = np.arange(ny) / (ny - 1.0)
+    s, Ta = couette_mu_profile(xi, Ma, Pr)
+    ux, T = m["ux"][:, 0] / U0, m["T"][:, 0]
+    # measured: 1.1e-3 on u (an O(Ma^2) error of the lattice model, 1.0e-3 at
+    # Pr = 0.71 as well) and 3.1e-3 on the heating T - T0
+    assert _rel(ux, s) < 2e-3
+    assert _rel(T, Ta, 1.0) < 6e-3
+    # the viscosity law matters: constant viscosity would give u = U0 xi,
+    # 14x farther from this result than the closed form is
+    assert _rel(ux, xi) > 5 * _rel(ux, s)
+    # adiabatic wall: the heating peaks there; uniform pressure across
+    assert int(np.argmax(T)) == 0 and abs(T[0] / Ta[0] - 1) < 1e-3
+    assert np.ptp(m["p"][:, 0]) < 1e-5
+    assert np.abs(m["uy"][:, 0]).max() < 1e-8 * U0
+
+
+def test_high_prandtl_grid_modes_unstable(orc):
+    # A stability property of the model at these parameters (tau0 = 0.8,
+    # varsigma/nu = 1, gamma1 = -2, gamma2 = 2), not of any implementation: at
+    # Pr = 20 the heat-flux rate sigma_j = 1 / (1/2 + 3 mu / (Pr rho0)) is
+    # 1.94, close to 2, and x-dependent grid-scale perturbations of the
+    # variable-viscosity Couette flow grow.  The x-invariant flow never
+    # excites them (it stays exactly x-invariant); white noise of 1e-8 on the
+    # DFs blows up within a few hundred steps, while at Pr = 0.71 it decays.
+    def run(Pr, amp, steps):
+        cfg = W.couette_variable_mu(nx=4, ny=32, Ma_e=0.1, Pr=Pr)
+        o = orc.Oracle(cfg, threads=8)
+        if amp:
+            nf, ng = W.df_noise(4, 32, 7, amp)
+            f, g = o.get_state()
+            o.set_state(f + nf, g + ng)
+        st = o.step(steps)
+        return st, o.macros() if st == 0 else None
+    st, _ = run(20.0, 1e-8, 1000)
+    assert st != 0                                  # non-finite state reported
+    st, m = run(20.0, 0.0, 1000)
+    assert st == 0 and np.ptp(m["ux"], axis=1).max() == 0.0
+    cfg = W.couette_variable_mu(nx=4, ny=32, Ma_e=0.1, Pr=0.71)
+    o = orc.Oracle(cfg, threads=8)
+    nf, ng = W.df_noise(4, 32, 7, 1e-8)
+    f, g = o.get_state()
+    o.set_state(f + nf, g + ng)
+    xdev = []
+    for n in (1000, 3000):
+        assert o.step(n) == 0
+        xdev.append(np.ptp(o.macros()["ux"], axis=1).max())
+    assert xdev[0] < 1e-8 and xdev[1] < 0.2 * xdev[0]  # measured 1.7e-9, then 1.0e-10
 
 
 def _poiseuille(orc, ny, steps):
