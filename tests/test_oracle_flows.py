@@ -262,6 +262,32 @@ def test_couette_mach_order_and_corrections(orc):
     assert f2 > 10 * e2
 
 
+def test_extrapolation_order_accuracy(orc):
+    # Sec. 3 / Eq. (neq.extrapolation): thermal Couette flow (constant mu,
+    # both walls at T0, lid u = 0.05).  With second-order extrapolation the
+    # temperature error is at the Mach-number floor on every grid (measured
+    # 7.4e-5 and 9.9e-5 of the heating at 16 and 32 nodes); first-order
+    # extrapolation adds a spatial error of second order in the node spacing
+    # (3.8e-2 and 9.0e-3).
+    U = 0.05
+
+    def e_T(ny, order):
+        cfg = W.couette(nx=1, ny=ny, U=U)
+        for w in cfg["walls"][:2]:
+            w["extrap_order"] = order
+        o = orc.Oracle(cfg, threads=8)
+        d = o.derived()
+        assert o.step(int(12 * (ny - 1) ** 2 / 0.1)) == 0
+        xi = np.arange(ny) / (ny - 1.0)
+        Ta = 1 + 0.71 * U * U / (2 * d["Cp"]) * xi * (1 - xi)
+        return _rel(o.macros()["T"][:, 0], Ta, 1.0)
+
+    f16, f32 = e_T(16, 1), e_T(32, 1)
+    assert 1.8 < np.log2(f16 / f32) < 2.3
+    s16, s32 = e_T(16, 2), e_T(32, 2)
+    assert max(s16, s32) < 2e-4 and s32 < 0.05 * f32
+
+
 def test_high_prandtl_grid_modes_unstable(orc):
     # A stability property of the model at these parameters (tau0 = 0.8,
     # varsigma/nu = 1, gamma1 = -2, gamma2 = 2), not of any implementation: at
