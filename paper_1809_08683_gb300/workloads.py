@@ -77,14 +77,15 @@ def poiseuille_force(ny, U0, tau0, rho0=1.0):
 
 
 def poiseuille(nx=4, ny=128, U0=0.05, T=1.0, tau0=0.8, Pr=0.7, gamma=1.3,
-               eos=(EOS_CUBIC, (0.05, 0.2)), precision=0):
-    """Thermal Poiseuille flow, walls at rest at T, constant body force,
-    periodic in x, second-order extrapolation; default EOS is the cubic
+               eos=(EOS_CUBIC, (0.05, 0.2)), precision=0, Th=None):
+    """Thermal Poiseuille flow, walls at rest, lower wall at T (= T_c) and
+    upper wall at Th (default T), constant body force, periodic in x,
+    second-order extrapolation; default EOS is the cubic
     rho R T/(1 - b rho) - a rho^2 with a = 0.05, b = 0.2."""
     Fx = poiseuille_force(ny, U0, tau0)
     return base(nx, ny, tau0=tau0, Pr=Pr, gamma=gamma, precision=precision,
                 force=(Fx, 0.0), force_mode=0,
-                walls=[wall((0, 0), T, 0, 2), wall((0, 0), T, 0, 2), periodic(), periodic()],
+                walls=[wall((0, 0), T, 0, 2), wall((0, 0), T if Th is None else Th, 0, 2), periodic(), periodic()],
                 eos={"kind": int(eos[0]), "params": list(eos[1])})
 
 

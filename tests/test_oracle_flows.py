@@ -11,7 +11,7 @@ import pytest
 
 from paper_1809_08683_gb300 import workloads as W
 
-from closed_forms import couette_mu_profile
+from closed_forms import couette_mu_profile, cs_pressure, uniform_pressure_density
 
 EX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1], dtype=float)
 EY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1], dtype=float)
@@ -232,6 +232,56 @@ def test_couette_variable_viscosity_closed_form(orc):
     assert int(np.argmax(T)) == 0 and abs(T[0] / Ta[0] - 1) < 1e-3
     assert np.ptp(m["p"][:, 0]) < 1e-5
     assert np.abs(m["uy"][:, 0]).max() < 1e-8 * U0
+
+
+@pytest.mark.parametrize("eos", [W.EOS_DECOUPLING, W.EOS_IDEAL, W.EOS_CS])
+def test_poiseuille_unequal_wall_temperatures(orc, eos):
+    # Sec. 4.1: lower wall at T_c = T0 = 1, upper at T_h, Pr = 0.71, Ec = 1,
+    # lattice Ma = U0 / c_s = 0.2, 64 nodes across, C_p = 3.5 c_s^2 / T0
+    # (Eq. Cp; gamma = 1.4, or 1.101465 for Carnahan-Starling).  Eq.
+    # (Poiseuille.u.T): u / U0 = 4 xi (1 - xi), (T - T_c) / (T_h - T_c) =
+    # (Pr Ec / 3)[1 - (1 - 2 xi)^4] + xi.  Density (Eq. rho.analytical): 1
+    # for the decoupling EOS, A T0 / T for the ideal gas, uniform pressure
+    # with the initial mass for Carnahan-Starling.  Measured: E_u 1.7e-3,
+    # E_T 6.3e-4 for every EOS; density within 5e-5 (0.4% and 1.2% of its
+    # variation for the ideal gas and Carnahan-Starling).
+    ny, Pr, Ec = 64, 0.71, 1.0
+    U0 = 0.2 * np.sqrt(1.0 / 3.0)
+    gamma = 1.101465 if eos == W.EOS_CS else 1.4
+    cp = orc.Oracle(W.poiseuille(nx=1, ny=ny, U0=U0, Pr=Pr, gamma=gamma, eos=(eos, ())), threads=1).derived()["Cp"]
+    assert abs(cp - 3.5 / 3.0) < 1e-5
+    dT = U0 * U0 / (cp * Ec)
+    cfg = W.poiseuille(nx=1, ny=ny, U0=U0, Pr=Pr, gamma=gamma, eos=(eos, ()), Th=1.0 + dT)
+    o = orc.Oracle(cfg, threads=8)
+    d = o.derived()
+    assert o.step(60000) == 0
+    m = o.macros()
+    xi = np.arange(ny) / (ny - 1.0)
+    ua = 4 * xi * (1 - xi)
+    tha = Pr * Ec / 3 * (1 - (1 - 2 * xi) ** 4) + xi
+    assert _rel(m["ux"][:, 0] / U0, ua) < 3e-3
+    assert _rel((m["T"][:, 0] - 1.0) / dT, tha) < 1.5e-3
+    rho = m["rho"][:, 0]
+    assert abs(rho.mean() - 1.0) < 1e-10                      # mass of the initial state
+    Ta = 1.0 + dT * tha
+    if eos == W.EOS_DECOUPLING:
+        rho_a = np.ones(ny)
+    elif eos == W.EOS_IDEAL:
+        rho_a = (1.0 / Ta) / (1.0 / Ta).mean()
+    else:
+        b = np.sqrt(2.0) * np.pi / 3.0                        # b = sqrt(2) pi / (3 rho_r), Sec. 4
+        rho_a = uniform_pressure_density(Ta, 1.0, lambda r, t: cs_pressure(r, t, d["R"], b), rho_max=2.0)
+    err = np.abs(rho - rho_a).max()
+    assert err < 1e-4
+    if eos != W.EOS_DECOUPLING:
+        assert err < 0.03 * np.ptp(rho_a)
+
+
+def test_uniform_pressure_density_ideal_gas():
+    # the bisection helper reproduces the ideal-gas closed form rho ~ 1 / T
+    T = 1.0 + 0.05 * np.sin(np.linspace(0.0, 3.0, 40)) ** 2
+    rho = uniform_pressure_density(T, 1.0, lambda r, t: r * t / 3.0)
+    assert np.abs(rho - (1.0 / T) / (1.0 / T).mean()).max() < 1e-12
 
 
 def test_couette_mach_order_and_corrections(orc):
