@@ -243,6 +243,23 @@ def serving_run(n, dev):
     return served
 
 
+def max_over_ranks(value, world, dist=None, device=None):
+    """The largest of a per-rank float over all ranks (all_reduce MAX), the
+    bench's rule for timed regions; `value` itself when world == 1."""
+    if world <= 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(nodes_per_rank, time_steps, world, ms):
+    """Whole-job lattice updates per second (millions): every rank advances
+    its own replica of the workload, over the slowest rank's time."""
+    return nodes_per_rank * time_steps * world / (ms * 1e-3) / 1e6
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -328,12 +345,9 @@ def main():
     ms = ev0.elapsed_time(ev1)
     for lat in lats:        # a run that produced NaN/Inf is not a measurement
         lat.sync()
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dist, dev)
     steps_total = args.steps * chunk
-    value = nodes * steps_total * world / (ms * 1e-3) / 1e6
+    value = whole_job_mlups(nodes, steps_total, world, ms)
     clocks = clk.summary()
 
     # fused kernel against the HBM roofline
@@ -374,7 +388,8 @@ def main():
             e2e_step()
         barrier()
         el = time.perf_counter() - t0
-        e2e = {"value": nodes * chunk * args.e2e_steps * world / el / 1e6, "unit": "MLUPS",
+        el = max_over_ranks(el, world, dist, dev)
+        e2e = {"value": whole_job_mlups(nodes, chunk * args.e2e_steps, world, el * 1e3), "unit": "MLUPS",
                "h2d_bytes_per_step": nodes * 4 * 8, "d2h_bytes_per_step": nodes * 5 * 8}
 
     cpu = None

@@ -1,0 +1,54 @@
+"""Host-side rules of bench.py's multi-rank path, on two CPU ranks (gloo):
+the timed region's duration is the slowest rank's, the whole-job rate counts
+every rank's replica of the workload, and the reference arm runs on rank 0
+only.  No GPU is involved."""
+import os
+import socket
+
+import pytest
+
+import bench
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, outdir):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ms = bench.max_over_ranks(10.0 + 5.0 * rank, world, dist, "cpu")
+        rate = bench.whole_job_mlups(1000, 100, world, ms)
+        with open(os.path.join(outdir, f"r{rank}"), "w") as fh:
+            fh.write(f"{ms!r} {rate!r}")
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_rate_two_ranks(tmp_path):
+    import torch.multiprocessing as mp
+    world = 2
+    mp.spawn(_rank_main, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    for rank in range(world):
+        ms, rate = (float(v) for v in (tmp_path / f"r{rank}").read_text().split())
+        assert ms == 15.0                                   # the slower rank's time
+        assert rate == pytest.approx(1000 * 100 * 2 / 15e-3 / 1e6)
+
+
+def test_single_rank_needs_no_process_group():
+    assert bench.max_over_ranks(3.5, 1) == 3.5
+    assert bench.whole_job_mlups(10, 20, 1, 2.0) == pytest.approx(10 * 20 / 2e-3 / 1e6)
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
+    import sys
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"])
+    assert bench.run_reference(bench.parse()) == 0        # no oracle work, no line
+    assert capsys.readouterr().out == ""
