@@ -134,7 +134,7 @@ def test_thermal_wave_decay_gives_conductivity(orc, tau, Pr):
 
 
 @pytest.mark.parametrize("eos,gamma", [((W.EOS_IDEAL, ()), 1.4), ((W.EOS_CUBIC, (0.05, 0.2)), 1.3),
-                                       ((W.EOS_DECOUPLING, ()), 1.4)])
+                                       ((W.EOS_DECOUPLING, ()), 1.4), ((W.EOS_CS, ()), 1.101465)])
 def test_sound_speed(orc, eos, gamma):
     # linear acoustics of the recovered equations: with rho Cv DT/Dt = -p div u,
     # c^2 = (dp/drho)_T + (dp/dT)_rho p0 / (rho0^2 Cv); ideal gas: gamma R T0
@@ -149,7 +149,12 @@ def test_sound_speed(orc, eos, gamma):
     a = _mode_amplitude_series(o, "rho", np.cos(k * x)[None], 1600, 1)
     t = np.arange(a.size, dtype=float)
     R = d["R"]
-    pT = {W.EOS_IDEAL: R, W.EOS_CUBIC: R / (1 - 0.2), W.EOS_DECOUPLING: 0.0}[eos[0]]
+    # (dp/dT)_rho at (rho0, T0) = (1, 1): R, R / (1 - b) for the cubic EOS,
+    # 0 for decoupling, Z(b / 4) R for Carnahan-Starling (Eq. EOSs.3, b =
+    # sqrt(2) pi / (3 rho0))
+    e0 = np.sqrt(2.0) * np.pi / 12.0
+    z0 = (1 + e0 + e0 ** 2 - e0 ** 3) / (1 - e0) ** 3
+    pT = {W.EOS_IDEAL: R, W.EOS_CUBIC: R / (1 - 0.2), W.EOS_DECOUPLING: 0.0, W.EOS_CS: z0 * R}[eos[0]]
     c = np.sqrt(1 / 3 + pT * d["p0"] / d["Cv"])
 
     def model(t, A, w, ph, G, B, K):
