@@ -71,7 +71,13 @@ typedef struct {
     int32_t precision;    /* lbm_precision */
     int32_t visc_law;     /* 0 constant mu, 1 mu = mu0 T/T0, 2 Sutherland */
     double rho0, T0;      /* reference state */
-    double Pr;            /* Prandtl number Cp mu / lambda (Sec. 2.2) */
+    double Pr;            /* Prandtl number Cp mu / lambda (Sec. 2.2).  High Pr puts
+                           * sigma_j = 1 / (1/2 + 3 mu / (Pr rho0)) near 2, where the
+                           * scheme's grid-scale modes grow: with tau0 = 0.8 and the
+                           * paper's varpi, gamma1, gamma2, from Pr = 3 in a sheared
+                           * channel and by Pr = 20 at rest.  A flow that stays exactly
+                           * x-invariant never excites them; FP32 storage's stochastic
+                           * rounding, whose draws depend on x, does. */
     double gamma;         /* Cp / Cv with Cp - Cv = p0 / (rho0 T0) */
     double tau0;          /* 1/s_p at (rho0, T0): mu0 = rho0 (tau0 - 1/2) / 3 */
     double visc_p[2];     /* Sutherland: visc_p[0] = S / T0 (ratio form of Sec. 4.3) */
