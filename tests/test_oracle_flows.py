@@ -233,6 +233,12 @@ def test_couette_variable_viscosity_closed_form(orc):
     # the viscosity law matters: constant viscosity would give u = U0 xi,
     # 14x farther from this result than the closed form is
     assert _rel(ux, xi) > 5 * _rel(ux, s)
+    # ideal gas at uniform pressure: rho / rho_r = A T0 / T with
+    # A = 1 + Pr Ma_e^2 / 3 (Sec. 4.2; measured within 0.8% of the density's
+    # variation, about 0.6% of which is A's continuous mean against the
+    # lattice's discrete one)
+    rho_a = (1.0 + Pr * Ma * Ma / 3.0) / Ta
+    assert np.abs(m["rho"][:, 0] - rho_a).max() < 0.02 * np.ptp(rho_a)
     # adiabatic wall: the heating peaks there; uniform pressure across
     assert int(np.argmax(T)) == 0 and abs(T[0] / Ta[0] - 1) < 1e-3
     assert np.ptp(m["p"][:, 0]) < 1e-5
