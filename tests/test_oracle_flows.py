@@ -295,6 +295,31 @@ def test_uniform_pressure_density_ideal_gas():
     assert np.abs(rho - (1.0 / T) / (1.0 / T).mean()).max() < 1e-12
 
 
+def test_poiseuille_mach_order(orc):
+    # Sec. 4.1 (Fig. Poiseuille.Ma): Ec = 100 Ma^2 keeps T_h - T_c fixed while
+    # the lattice Mach number Ma = U0 / c_s varies; the velocity error is
+    # fourth order in Ma when Ma is large and falls towards second order when
+    # it is small.  Measured (64 nodes, Pr = 0.71, ideal gas): E_u = 1.77e-6,
+    # 9.86e-6 at Ma = 0.02, 0.04 (order 2.48) and 7.50e-4, 1.05e-2 at Ma =
+    # 0.16, 0.32 (order 3.81).
+    ny, Pr, cp = 64, 0.71, 3.5 / 3.0
+    xi = np.arange(ny) / (ny - 1.0)
+    ua = 4 * xi * (1 - xi)
+
+    def e_u(Ma_l):
+        U0 = Ma_l * np.sqrt(1.0 / 3.0)
+        dT = U0 * U0 / (cp * 100 * Ma_l ** 2)
+        cfg = W.poiseuille(nx=1, ny=ny, U0=U0, Pr=Pr, gamma=1.4, eos=(W.EOS_IDEAL, ()), Th=1.0 + dT)
+        o = orc.Oracle(cfg, threads=8)
+        assert abs(o.derived()["Cp"] - cp) < 1e-9
+        assert o.step(60000) == 0
+        return _rel(o.macros()["ux"][:, 0] / U0, ua)
+
+    small = np.log2(e_u(0.04) / e_u(0.02))
+    large = np.log2(e_u(0.32) / e_u(0.16))
+    assert 3.5 < large < 4.3 and small < 3.0 and large > small + 0.8
+
+
 def test_couette_mach_order_and_corrections(orc):
     # Sec. 4.2 (Fig. Couette.Ma): in the variable-viscosity Couette flow the
     # velocity error E_u of Eq. (Err) is fourth order in the lattice Mach
