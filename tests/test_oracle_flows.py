@@ -295,6 +295,47 @@ def test_uniform_pressure_density_ideal_gas():
     assert np.abs(rho - (1.0 / T) / (1.0 / T).mean()).max() < 1e-12
 
 
+def _poiseuille_ec(orc, Pr, Ec, eos, gamma, steps):
+    # Sec. 4.1 set-up at lattice Ma = 0.2, 64 nodes, C_p = 3.5 c_s^2 / T0:
+    # T_h - T_c = U0^2 / (C_p Ec); returns the oracle's step status and, when
+    # it ran, E_u and E_T of Eq. (Err) against Eq. (Poiseuille.u.T)
+    ny, cp = 64, 3.5 / 3.0
+    U0 = 0.2 * np.sqrt(1.0 / 3.0)
+    dT = U0 * U0 / (cp * Ec)
+    cfg = W.poiseuille(nx=1, ny=ny, U0=U0, Pr=Pr, gamma=gamma, eos=(eos, ()), Th=1.0 + dT)
+    o = orc.Oracle(cfg, threads=8)
+    st = o.step(steps)
+    if st != 0:
+        return st, None, None
+    m = o.macros()
+    xi = np.arange(ny) / (ny - 1.0)
+    ua = 4 * xi * (1 - xi)
+    tha = Pr * Ec / 3 * (1 - (1 - 2 * xi) ** 4) + xi
+    return st, _rel(m["ux"][:, 0] / U0, ua), _rel((m["T"][:, 0] - 1.0) / dT, tha)
+
+
+@pytest.mark.parametrize("Pr,Ec,steps", [(0.71, 0.1, 60000), (0.71, 100.0, 60000), (4.0, 10.0, 300000)])
+def test_poiseuille_pr_ec_sweep(orc, Pr, Ec, steps):
+    # Fig. Poiseuille.u.T: Pr = 0.71 with Ec from 0.1 to 100, and Ec = 10 with
+    # Pr up to 4 (the viscous-heating term Pr Ec / 3 from 0.02 to 24).
+    # Measured E_T: 7.9e-5, 2.3e-3 and 7.3e-4; E_u 1.7e-3 throughout.
+    st, eu, et = _poiseuille_ec(orc, Pr, Ec, W.EOS_IDEAL, 1.4, steps)
+    assert st == 0 and eu < 2.5e-3 and et < 4e-3
+
+
+def test_poiseuille_pr01_loses_stability_with_the_ideal_gas_only(orc):
+    # Sec. 4.1 reports that the Ec = 10, Pr = 0.1 case loses numerical
+    # stability for the ideal-gas EOS (and not for the others).  The oracle
+    # does the same: the ideal gas turns non-finite within 1000 steps, while
+    # the decoupling and Carnahan-Starling EOS run on and match the closed
+    # form (measured E_u 1.7e-3, E_T 5.0e-3).
+    st, _, _ = _poiseuille_ec(orc, 0.1, 10.0, W.EOS_IDEAL, 1.4, 3000)
+    assert st != 0
+    for eos, gamma in ((W.EOS_DECOUPLING, 1.4), (W.EOS_CS, 1.101465)):
+        st, eu, et = _poiseuille_ec(orc, 0.1, 10.0, eos, gamma, 60000)
+        assert st == 0 and eu < 2.5e-3 and et < 8e-3, (eos, eu, et)
+
+
 def test_poiseuille_mach_order(orc):
     # Sec. 4.1 (Fig. Poiseuille.Ma): Ec = 100 Ma^2 keeps T_h - T_c fixed while
     # the lattice Mach number Ma = U0 / c_s varies; the velocity error is
