@@ -361,6 +361,26 @@ def test_poiseuille_mach_order(orc):
     assert 3.5 < large < 4.3 and small < 3.0 and large > small + 0.8
 
 
+def test_couette_pr01_loses_stability_with_the_ideal_gas(orc):
+    # Sec. 4.2 reports that the variable-viscosity Couette flow at Ma_e = 0.1,
+    # Pr = 0.1 loses numerical stability for the ideal-gas EOS.  The oracle
+    # does the same (non-finite within 1000 steps), while with the decoupling
+    # EOS it runs on and matches the closed form (measured E_u 1.0e-3,
+    # E_T 2.8e-3).
+    def cfg(eos):
+        return W.couette_variable_mu(nx=1, ny=32, Ma_e=0.1, Pr=0.1, eos=(eos, ()))
+
+    assert orc.Oracle(cfg(W.EOS_IDEAL), threads=8).step(3000) != 0
+    c = cfg(W.EOS_DECOUPLING)
+    o = orc.Oracle(c, threads=8)
+    assert o.step(40000) == 0
+    U0 = c["walls"][1]["u"][0]
+    s, Ta = couette_mu_profile(np.arange(32) / 31.0, U0 / np.sqrt(o.derived()["Cp"]), 0.1)
+    m = o.macros()
+    assert _rel(m["ux"][:, 0] / U0, s) < 2e-3
+    assert _rel(m["T"][:, 0], Ta, 1.0) < 6e-3
+
+
 def test_couette_mach_order_and_corrections(orc):
     # Sec. 4.2 (Fig. Couette.Ma): in the variable-viscosity Couette flow the
     # velocity error E_u of Eq. (Err) is fourth order in the lattice Mach
