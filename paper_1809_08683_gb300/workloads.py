@@ -53,14 +53,18 @@ def couette(nx=4, ny=64, U=0.05, T=1.0, tau0=0.8, Pr=0.71, gamma=1.4, precision=
                 eos={"kind": EOS_IDEAL, "params": []})
 
 
-def couette_variable_mu(nx=1, ny=32, Ma_e=0.1, tau0=0.8, Pr=0.71, gamma=1.4, eos=(EOS_IDEAL, ()), precision=0):
+def couette_variable_mu(nx=1, ny=32, Ma_e=0.1, tau0=0.8, Pr=0.71, gamma=1.4, eos=(EOS_IDEAL, ()), precision=0,
+                        cp=None):
     """Thermal Couette flow with mu / mu0 = T / T0 (Sec. 4.2): adiabatic lower
     wall at rest (south, Neumann), upper wall moving at u = (U0, 0) and held
     at T0 = 1 (north, Dirichlet), periodic in x, second-order extrapolation,
-    tau0 = 0.8 for mu0.  U0 = Ma_e sqrt(Cp T0) with Cp = gamma / (gamma - 1)
-    c_s^2 / T0, the heat capacity of the ideal and decoupling EOS at
-    rho0 = T0 = 1."""
-    cp = gamma / (gamma - 1.0) / 3.0
+    tau0 = 0.8 for mu0.  U0 = Ma_e sqrt(Cp T0).  cp is the heat capacity the
+    configuration produces; the default, gamma / (gamma - 1) c_s^2 / T0, is
+    that of the ideal and decoupling EOS at rho0 = T0 = 1.  For another EOS
+    pass it (the paper's Eq. Cp gives 3.5 c_s^2 / T0 = 7/6 with the gamma
+    it quotes for each EOS)."""
+    if cp is None:
+        cp = gamma / (gamma - 1.0) / 3.0
     U0 = Ma_e * math.sqrt(cp)
     return base(nx, ny, tau0=tau0, Pr=Pr, gamma=gamma, precision=precision, visc_law=VISC_LINEAR,
                 walls=[wall((0, 0), 1.0, 1, 2), wall((U0, 0), 1.0, 0, 2), periodic(), periodic()],

@@ -361,6 +361,29 @@ def test_poiseuille_mach_order(orc):
     assert 3.5 < large < 4.3 and small < 3.0 and large > small + 0.8
 
 
+def test_couette_u_and_T_independent_of_the_eos(orc):
+    # Sec. 4.2: the u and T profiles of the variable-viscosity Couette flow
+    # are the same for every EOS (they depend on Pr and Ma_e only), while the
+    # density is not.  Ideal gas, decoupling and Carnahan-Starling at
+    # C_p = 3.5 c_s^2 / T0 (Eq. Cp), Pr = 0.71, Ma_e = 0.1: measured u within
+    # 3e-6 U0 and T within 1e-5 of the heating of the ideal-gas result, with
+    # density variations of 3.5e-3, 2e-7 and 1.1e-3.
+    res = {}
+    for eos, gamma in ((W.EOS_IDEAL, 1.4), (W.EOS_DECOUPLING, 1.4), (W.EOS_CS, 1.101465)):
+        cfg = W.couette_variable_mu(nx=1, ny=32, Ma_e=0.1, Pr=0.71, eos=(eos, ()), gamma=gamma, cp=3.5 / 3.0)
+        o = orc.Oracle(cfg, threads=8)
+        assert abs(o.derived()["Cp"] - 3.5 / 3.0) < 1e-5
+        assert o.step(40000) == 0
+        m = o.macros()
+        res[eos] = (m["ux"][:, 0] / cfg["walls"][1]["u"][0], m["T"][:, 0], m["rho"][:, 0])
+    u0, T0, rho0 = res[W.EOS_IDEAL]
+    heating = T0.max() - 1.0
+    for eos in (W.EOS_DECOUPLING, W.EOS_CS):
+        u, T, rho = res[eos]
+        assert np.abs(u - u0).max() < 2e-5 and np.abs(T - T0).max() < 1e-4 * heating
+        assert abs(np.ptp(rho) - np.ptp(rho0)) > 0.2 * np.ptp(rho0)
+
+
 def test_couette_pr01_loses_stability_with_the_ideal_gas(orc):
     # Sec. 4.2 reports that the variable-viscosity Couette flow at Ma_e = 0.1,
     # Pr = 0.1 loses numerical stability for the ideal-gas EOS.  The oracle
