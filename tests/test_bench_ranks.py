@@ -1,7 +1,7 @@
-"""Host-side rules of bench.py's multi-rank path, on two CPU ranks (gloo):
-the timed region's duration is the slowest rank's, the whole-job rate counts
-every rank's replica of the workload, and the reference arm runs on rank 0
-only.  No GPU is involved."""
+"""Host-side rules of bench.py, without a GPU: on two CPU ranks (gloo) the
+timed region's duration is the slowest rank's and the whole-job rate counts
+every rank's replica of the workload; the reference arm runs on rank 0 only;
+the clock record reports the median SM clock and the throttle reasons seen."""
 import os
 import socket
 
@@ -52,3 +52,26 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"])
     assert bench.run_reference(bench.parse()) == 0        # no oracle work, no line
     assert capsys.readouterr().out == ""
+
+
+def test_clock_summary_reads_samples_and_reasons(tmp_path):
+    # nvidia-smi --format=csv,noheader,nounits lines: sm, max sm, power,
+    # hw_slowdown, hw_thermal_slowdown, sw_thermal_slowdown, sw_power_cap
+    c = bench.Clocks(0)
+    c.path = str(tmp_path / "clocks.csv")
+    c.proc = object()                                   # as if the sampler ran
+    (tmp_path / "clocks.csv").write_text(
+        "2070, 2070, 950.1, Not Active, Not Active, Not Active, Not Active\n"
+        "1980, 2070, 1399.8, Not Active, Not Active, Not Active, Active\n"
+        "[N/A], 2070, 0.0, Not Active, Not Active, Not Active, Not Active\n"
+        "2055, 2070, 1200.0, Not Active, Not Active, Not Active, Not Active\n")
+    s = c.summary()
+    assert s["sm_mhz"] == 2055.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]             # kept and noted, not a rejection reason
+
+
+def test_clock_summary_without_a_sampler():
+    with bench.Clocks(0) as c:                          # no nvidia-smi here, or no GPU behind it
+        pass
+    s = c.summary()
+    assert s["sm_mhz"] is None and s["reasons"]
