@@ -75,3 +75,26 @@ def test_clock_summary_without_a_sampler():
         pass
     s = c.summary()
     assert s["sm_mhz"] is None and s["reasons"]
+
+
+def test_traffic_figure_follows_the_kernel_code_not_its_comments(tmp_path, monkeypatch):
+    import shutil
+    src = tmp_path / "paper_1809_08683_gb300" / "csrc"
+    src.mkdir(parents=True)
+    for name in bench.KERNEL_SOURCES:
+        shutil.copy(os.path.join(bench.ROOT, "paper_1809_08683_gb300", "csrc", name), src / name)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h = bench.kernel_source_hash()
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic_demo.txt").write_text(
+        f"# a summary\nkernel = k_demo\nworkload = demo\nsource_sha256 = {h}\ndram_bytes_per_launch = 12345\n")
+    assert bench.read_traffic("demo", "k_demo") == 12345.0
+    assert bench.read_traffic("demo", "k_other") is None and bench.read_traffic("other", "k_demo") is None
+    first = src / bench.KERNEL_SOURCES[0]
+    text = first.read_text()
+    first.write_text("// a new comment line\n" + text.replace("\n", "\n  ", 3) + "\n/* block */\n")
+    assert bench.kernel_source_hash() == h                # comments and blank space do not count
+    assert bench.read_traffic("demo", "k_demo") == 12345.0
+    first.write_text(text + "\nstatic int changed_code = 1;\n")
+    assert bench.kernel_source_hash() != h
+    assert bench.read_traffic("demo", "k_demo") is None    # the stored figure no longer applies
