@@ -146,6 +146,41 @@ lbm_status lbm_init_macros(lbm_ctx* ctx, const double* rho, const double* ux,
 /* Derived constants: R, Cv, Cp, mu0, p0, eta0, lambda0, c_s^2. */
 lbm_status lbm_derived(const lbm_ctx* ctx, double* out8);
 
+/* Rounding of the FP32-deviation stores (no effect with FP64 storage).
+ * LBM_ROUND_STOCHASTIC (the default after lbm_create): each stored value
+ * gets uniform noise of one unit in its last place before rounding, so the
+ * expected stored value is the exact one and a nearly steady state does not
+ * stall on a repeated rounding error; the noise comes from a counter-based
+ * hash of (node, step), so results are reproducible and the same alone or
+ * batched.  It leaves a floor of about 1e-6 on the residual of
+ * lbm_diagnostics.  LBM_ROUND_NEAREST: plain round-to-nearest, a
+ * deterministic map.  The paper states no precision (Sec. 2 uses exact
+ * arithmetic); both modes are this library's.  Takes effect from the next
+ * step, also inside existing batches and their graphs; asynchronous on the
+ * context's stream.  LBM_EINVAL for another mode. */
+typedef enum { LBM_ROUND_STOCHASTIC = 0, LBM_ROUND_NEAREST = 1 } lbm_rounding;
+lbm_status lbm_set_rounding(lbm_ctx* ctx, int mode);
+
+/* Copy the state of src into dst, converting the storage precision (FP64 <->
+ * FP32 deviations): both contexts must describe the same problem (identical
+ * configurations apart from precision, the same EOS) and be initialised.
+ * dst takes src's step count, so the residual snapshot of
+ * lbm_diagnostics (also copied) and the stochastic rounding continue where
+ * src left off.  Synchronises both streams.  The paper has no counterpart:
+ * it lets a solve started in FP32 storage finish in FP64 once FP32 reaches
+ * its residual floor.  LBM_EINVAL if the problems differ. */
+lbm_status lbm_copy_state(lbm_ctx* dst, const lbm_ctx* src);
+
+/* Check of the bounded-wait path of the fused kernels: one device thread
+ * waits on an mbarrier that no copy will complete, gives up after
+ * limit_cycles SM cycles (0 .. 2^32; the fused kernels use 2^32), and
+ * records the timeout in the context's status word exactly as a fused
+ * kernel whose row copy never landed does.  Returns LBM_ETIMEOUT, which is
+ * then sticky on the context until lbm_set_eos(), lbm_init_macros() or
+ * lbm_set_state() re-initialises it.  Synchronises.  The paper has no
+ * counterpart; LBM_EINVAL for a limit outside the range. */
+lbm_status lbm_wait_selftest(lbm_ctx* ctx, long long limit_cycles);
+
 /* Launch shape of the fused kernel: one CTA per strip of bx columns and by
  * rows (>= 1).  pair = 0: one node per thread, bx = 32, 64 or 128.
  * pair = 1 or 2 (FP32 storage only): two neighbouring nodes per thread in
@@ -200,6 +235,20 @@ lbm_status lbm_batch_destroy(lbm_batch* b);     /* NULL-safe */
  * *ms_collide and *ms_wall receive their summed device times.  Synchronises. */
 lbm_status lbm_batch_step_profiled(lbm_batch* b, long nsteps, double* ms_collide, double* ms_wall);
 
+/* lbm_diagnostics for every member of a batch in one pass: one launch per
+ * storage precision over all members, one copy back and one
+ * synchronisation of the batch stream.  out8n (host, n x 8 doubles in the
+ * member order given to lbm_batch_create) receives each member's eight
+ * outputs as lbm_diagnostics defines them, bit for bit the values that
+ * lbm_diagnostics would return; snapshot != 0 stores every member's
+ * snapshot.  member_status (host, n entries, may be NULL) receives each
+ * member's status: LBM_OK, or the sticky LBM_EUNSTABLE / LBM_ETIMEOUT /
+ * LBM_ECUDA that lbm_diagnostics would return for it (its outputs are then
+ * NaN if it was already sticky).  The call itself fails only on bad
+ * arguments or a failed CUDA call.  The paper has no counterpart: it serves
+ * the residual checks of the serving loop. */
+lbm_status lbm_batch_diagnostics(lbm_batch* b, int snapshot, double* out8n, int* member_status);
+
 /* Conserved sums of a context's current state, computed without allocating
  * anything.  The paper has no counterpart: this entry point is for callers
  * that may not allocate device memory, for example a host program that
@@ -210,7 +259,8 @@ lbm_status lbm_batch_step_profiled(lbm_batch* b, long nsteps, double* ms_collide
  *   out4[0] total mass sum(rho), out4[1] sum(j_x), out4[2] sum(j_y),
  *   out4[3] sum over nodes of sum_i g_i (the total energy minus half the
  *   source work, so equal to the total energy when F = 0).
- * Asynchronous on the context's stream; the context's device must be current.
+ * Asynchronous on the context's stream; the context's device (the one
+ * current at lbm_create) must be current, else LBM_EINVAL.
  *
  * Scratch: block partials go to a file-scope static device array of 2048 x 4
  * doubles (64 KiB) that every GPU loading the library holds until exit.

@@ -75,6 +75,9 @@ int  orc_derived(const orc_ctx* c, double* out8); /* R, Cv, Cp, mu0, p0, eta0, l
 
 /* Boundary-pass-only hook: apply Sec. 3 at every wall node of the current state. */
 int  orc_boundary_pass(orc_ctx* c);
+/* grad(phi) of a field [ny][nx] at every node with the stencil of step 2
+ * (interior, walls, corners, periodic wraps), for the stencil's pins. */
+int  orc_grad_field(const orc_ctx* c, const double* phi, double* gx, double* gy);
 
 /* Node-level hooks for the algebraic pins. */
 /* m^eq, F_m, n^eq, Q_m at given (rho, u, T) and force (Fx, Fy). */

@@ -83,6 +83,7 @@ def lib():
             L.orc_set_threads.argtypes = [C.c_int]
             L.orc_derived.argtypes = [C.c_void_p, dp]
             L.orc_boundary_pass.argtypes = [C.c_void_p]
+            L.orc_grad_field.argtypes = [C.c_void_p, dp, dp, dp]
             L.orc_eq_moments.argtypes = [C.c_void_p] + [C.c_double] * 6 + [dp] * 4
             L.orc_matrix_M.argtypes = [dp]
             L.orc_matrix_Minv.argtypes = [dp]
@@ -206,6 +207,15 @@ class Oracle:
 
     def boundary_pass(self):
         self.L.orc_boundary_pass(self.h)
+
+    def grad_field(self, phi):
+        """(d phi/dx, d phi/dy) at every node with the oracle's gradient
+        stencil; phi is [ny][nx]."""
+        phi = np.ascontiguousarray(phi, dtype=np.float64)
+        gx, gy = np.empty_like(phi), np.empty_like(phi)
+        if self.L.orc_grad_field(self.h, _ptr(phi), _ptr(gx), _ptr(gy)) != 0:
+            raise RuntimeError("orc_grad_field failed")
+        return gx, gy
 
     def eq_moments(self, rho, ux, uy, T, Fx=0.0, Fy=0.0) -> dict:
         out = {k: np.empty(9) for k in ("meq", "Fm", "neq", "Qm")}

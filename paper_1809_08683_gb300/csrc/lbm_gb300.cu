@@ -152,7 +152,7 @@ __device__ __forceinline__ float ulp_scale(float v) { return __int_as_float(__fl
 struct AddDither {
     float r;
     mutable float s = 1.0f;  // sign of the next link's draw (folds to a constant once unrolled)
-    __device__ __forceinline__ explicit AddDither(uint32_t h) : r(dither_draw(h)) {}
+    __device__ __forceinline__ AddDither(uint32_t h, float scale) : r(dither_draw(h) * scale) {}
     __device__ __forceinline__ void operator()(float& f, float df, float& g, float dg) const {
         const float rs = s * r;
         f = f + fmaf(rs, ulp_scale(f), df);
@@ -246,6 +246,38 @@ __device__ __forceinline__ void push_pair(float* __restrict__ dst, const f2* v, 
                 o[(9 + i) * pl + off + 1] = v[9 + i].v.y;
             }
         }
+    } else if (act_b && !px && j >= 1 && j <= ny - 2 && (xa == 0 || xb == nx - 1)) {
+        // a pair holding one node of a walled x side, in a row away from the
+        // y walls: the wall node's populations that would leave the lattice
+        // land reversed in its own slots (Eqs. BB.f, BB.g), all others
+        // stream as in the interior
+        float* o = dst + ((long long)j * pitch + xa);
+        const int pl = (int)plane;
+        const bool west = xa == 0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int ex = (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+            const int ey = (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+            const int opp = (i == 0) ? 0 : (i <= 4 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5);
+            const int off = ey * pitch + ex;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int q = h ? 9 + i : i, qo = h ? 9 + opp : opp;
+                const float2 w = v[q].v;
+                if (ex == 0) {
+                    *reinterpret_cast<float2*>(o + q * pl + off) = w;
+                } else if (west && ex < 0) {
+                    o[qo * pl] = w.x;              // node a leaves through the west wall
+                    o[q * pl + off + 1] = w.y;     // node b lands on column 0
+                } else if (!west && ex > 0) {
+                    o[q * pl + off] = w.x;         // node a lands on column nx - 1
+                    o[qo * pl + 1] = w.y;          // node b leaves through the east wall
+                } else {
+                    o[q * pl + off] = w.x;
+                    o[q * pl + off + 1] = w.y;
+                }
+            }
+        }
     } else {
         // edge pair: per node, periodic wrap or bounce-back into its own slot
 #pragma unroll
@@ -318,13 +350,28 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait: gives up after about 2^32 SM cycles (2 s at 2 GHz).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait: gives up after `limit` SM cycles, by default 2^32 (2 s at
+// 2 GHz).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit = 1LL << 32) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > (1LL << 32)) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
+}
+
+// Check of the timeout path: one thread waits, with the given limit, on an
+// mbarrier that expects one arrival which nothing makes (no copy is issued),
+// gives up and sets the same status bit as a fused kernel whose row copy
+// never lands.
+__global__ void k_wait_selftest(unsigned int* status, long long limit) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait(&bar, 0, limit)) atomicOr(status, 2u);
 }
 
 // Global -> shared bulk copy completing on an mbarrier; addresses 16-byte
@@ -429,6 +476,7 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
     unsigned int* status = D->status;
     const uint32_t step_hash = mix32((uint32_t)(w.step0 + *counter) * 0x9e3779b1u + 0x632be5abu);
     __syncthreads();
+    const float dscale = (float)P.dither;
 
     const int x = w.x0 + tid;
     const bool active = x < nx;
@@ -603,7 +651,7 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
                 node_macros<MC>(P, v, mf);
                 if (!(isfinite(mf.rho_d) && isfinite(mf.T_d))) atomicOr(status, 1u);
             }
-            AddDither add(mix32(step_hash ^ ((uint32_t)j * 0x85ebca77u + (uint32_t)x * 0xc2b2ae3du)));
+            AddDither add(mix32(step_hash ^ ((uint32_t)j * 0x85ebca77u + (uint32_t)x * 0xc2b2ae3du)), dscale);
             // block strips keep the DFs in registers through the collision
             // (no spills at 128 registers; re-reading them cost 0.6%)
             lbm::collide<MC>(P, mf, v, v + 9, grx, gry, gpx, gpy, add);
@@ -688,6 +736,7 @@ __global__ void __launch_bounds__(32 * NW, WarpTraits<R>::WARPS_PER_SM / NW)
     unsigned int* status = D->status;
     const uint32_t step_hash = mix32((uint32_t)(w.step0 + *counter) * 0x9e3779b1u + 0x632be5abu);
     __syncthreads();  // parameters and barrier initialisation visible; the last block-wide barrier
+    const float dscale = (float)P.dither;
 
     const int wx0 = w.x0 + kWarpCols * wid;
     if (wx0 >= nx) return;  // whole warp beyond a ragged right edge
@@ -849,7 +898,7 @@ __global__ void __launch_bounds__(32 * NW, WarpTraits<R>::WARPS_PER_SM / NW)
             load_node(sc, v);
             Mac<R> mf;
             lbm::expand<MC>(P, mc, mf);
-            AddDither add(mix32(step_hash ^ ((uint32_t)j * 0x85ebca77u + (uint32_t)x * 0xc2b2ae3du)));
+            AddDither add(mix32(step_hash ^ ((uint32_t)j * 0x85ebca77u + (uint32_t)x * 0xc2b2ae3du)), dscale);
             // the DFs are fetched again for the final update, so that they
             // need not occupy registers through the collision
             auto reload = [&](R* f, R*) {
@@ -902,7 +951,7 @@ __device__ void broadcast_params(const Params<float>& a, Params<f2>& b) {
     BP(rho0); BP(T0); BP(E0); BP(Cv); BP(inv_Cv); BP(Rg); BP(eos_a); BP(eos_b); BP(p0); BP(rho0E0_p0);
     BP(rho0Cp0); BP(mu0); BP(inv_T0); BP(visc_S); BP(lam_fac); BP(tj_fac); BP(e_fac); BP(alpha1);
     BP(beta1); BP(alpha2); BP(beta2); BP(kk); BP(hh); BP(bb); BP(gamma1); BP(gamma2); BP(cR11);
-    BP(cR17); BP(cR18); BP(cR71); BP(cR77); BP(cR81); BP(cR88); BP(Fx); BP(Fy); BP(cs_b0);
+    BP(cR17); BP(cR18); BP(cR71); BP(cR77); BP(cR81); BP(cR88); BP(Fx); BP(Fy); BP(cs_b0); BP(dither);
 #undef BP
     b.eos = a.eos;
     b.visc = a.visc;
@@ -916,8 +965,8 @@ __device__ void broadcast_params(const Params<float>& a, Params<f2>& b) {
 struct AddDither2 {
     float2 r;
     mutable float s = 1.0f;
-    __device__ __forceinline__ explicit AddDither2(uint32_t h)
-        : r(make_float2(dither_draw(h), dither_draw(h + 0x9e3779b9u))) {}
+    __device__ __forceinline__ AddDither2(uint32_t h, float scale)
+        : r(make_float2(dither_draw(h) * scale, dither_draw(h + 0x9e3779b9u) * scale)) {}
     __device__ __forceinline__ void operator()(f2& f, f2 df, f2& g, f2 dg) const {
         const float2 rs = make_float2(s * r.x, s * r.y), rn = make_float2(-rs.x, -rs.y);
         f = f2(__fadd2_rn(f.v, __ffma2_rn(rs, make_float2(ulp_scale(f.v.x), ulp_scale(f.v.y)), df.v)));
@@ -966,6 +1015,7 @@ __global__ void __launch_bounds__(BX / 2, (KEEP ? LBM_PAIR_WARPS_PER_SM : 12) * 
     __syncthreads();
     if (tid == 0) broadcast_params(P1, P2);
     __syncthreads();
+    const float dscale = P1.dither;
 
     const int xa = w.x0 + 2 * tid, xb = xa + 1;
     const bool act_a = xa < nx, act_b = xb < nx;
@@ -1173,7 +1223,7 @@ __global__ void __launch_bounds__(BX / 2, (KEEP ? LBM_PAIR_WARPS_PER_SM : 12) * 
                 if (!(isfinite(mf.rho_d.v.x) && isfinite(mf.T_d.v.x) && (!act_b || (isfinite(mf.rho_d.v.y) && isfinite(mf.T_d.v.y)))))
                     atomicOr(status, 1u);
             }
-            AddDither2 add(mix32(step_hash ^ ((uint32_t)j * 0x85ebca77u + (uint32_t)xa * 0xc2b2ae3du)));
+            AddDither2 add(mix32(step_hash ^ ((uint32_t)j * 0x85ebca77u + (uint32_t)xa * 0xc2b2ae3du)), dscale);
             auto reload = [&](f2* f, f2* g) {
                 asm volatile("" ::: "memory");
 #pragma unroll
@@ -1260,6 +1310,7 @@ __global__ void __launch_bounds__(32 * NW, LBM_WARP2_WARPS_PER_SM / NW)
     __syncthreads();
     if (threadIdx.x == 0) broadcast_params(P1, P2);
     __syncthreads();  // the last block-wide barrier
+    const float dscale = P1.dither;
 
     const int wx0 = w.x0 + kWarp2Cols * wid;
     if (wx0 >= nx) return;
@@ -1456,7 +1507,7 @@ __global__ void __launch_bounds__(32 * NW, LBM_WARP2_WARPS_PER_SM / NW)
             load_pair((k + 1) % S, v);
             Mac<f2> mf;
             expand(P2, mc, mf);
-            AddDither2 add(mix32(step_hash ^ ((uint32_t)j * 0x85ebca77u + (uint32_t)xa * 0xc2b2ae3du)));
+            AddDither2 add(mix32(step_hash ^ ((uint32_t)j * 0x85ebca77u + (uint32_t)xa * 0xc2b2ae3du)), dscale);
             auto reload = [&](f2* f, f2*) {
                 asm volatile("" ::: "memory");
                 load_pair((k + 1) % S, f);  // f and g are v and v + 9: all 18 DFs
@@ -1676,6 +1727,20 @@ __global__ void k_set_plane(const InstDesc* D, int b, int q, double rest, const 
     }
 }
 
+// Plane-by-plane copy of a DF buffer into another context's buffer of the
+// same extents, converting the storage type (both hold deviations from the
+// same rest equilibrium).
+template <typename Rs, typename Rd>
+__global__ void k_copy_state(const Rs* __restrict__ src, long long splane, int spitch, Rd* __restrict__ dst,
+                             long long dplane, int dpitch, int nx, int ny) {
+    const long long nn = (long long)nx * ny, total = 18 * nn;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const long long q = i / nn, r = i - q * nn;
+        const int y = (int)(r / nx), x = (int)(r - (long long)y * nx);
+        dst[q * dplane + (long long)y * dpitch + x] = (Rd)src[q * splane + (long long)y * spitch + x];
+    }
+}
+
 // FP64 macros of one node of an R-typed buffer.
 template <typename R>
 __device__ __forceinline__ void macros_fp64(const InstDesc* D, const R* buf, int x, int y, Mac<double>& m) {
@@ -1723,11 +1788,13 @@ __device__ __forceinline__ double warp_max(double v) {
     return v;
 }
 
-// Per-block FP64 partial sums (slot 8 is a maximum) into partials[block][kDiagSlots].
+// Per-block FP64 partial sums (slot 8 is a maximum) into partials[block][kDiagSlots]:
+// block blk of nblk, grid-stride over the lattice's nodes.  k_diag and the
+// batched k_diag_batch run this with the same decomposition, so a lattice's
+// diagnostics are the same bits alone or batched.
 template <typename R>
-__global__ void __launch_bounds__(kDiagThreads) k_diag(const InstDesc* D, int b, double* __restrict__ snap,
-                                                       int take_snapshot, int have_snapshot,
-                                                       double* __restrict__ partials) {
+__device__ __forceinline__ void diag_partials(const InstDesc* D, int b, double* __restrict__ snap, int take_snapshot,
+                                              int have_snapshot, double* __restrict__ partials, int blk, int nblk) {
     const long long nn = (long long)D->nx * D->ny;
     const R* buf = reinterpret_cast<const R*>(D->buf[b]);
     double acc[kDiagSlots];
@@ -1735,8 +1802,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(const InstDesc* D, int b,
     for (int s = 0; s < kDiagSlots; ++s) acc[s] = 0.0;
     const double Lx = D->px ? (double)D->nx : (double)(D->nx - 1);
     const double Ly = D->py ? (double)D->ny : (double)(D->ny - 1);
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn;
-         t += (long long)gridDim.x * blockDim.x) {
+    for (long long t = blk * (long long)blockDim.x + threadIdx.x; t < nn; t += (long long)nblk * blockDim.x) {
         const int y = (int)(t / D->nx), x = (int)(t % D->nx);
         Mac<double> m;
         macros_fp64(D, buf, x, y, m);
@@ -1776,8 +1842,31 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(const InstDesc* D, int b,
         const int s = threadIdx.x;
         double v = red[0][s];
         for (int k = 1; k < kDiagThreads / 32; ++k) v = (s == 8) ? fmax(v, red[k][s]) : v + red[k][s];
-        partials[blockIdx.x * kDiagSlots + s] = v;
+        partials[blk * kDiagSlots + s] = v;
     }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kDiagThreads) k_diag(const InstDesc* D, int b, double* __restrict__ snap,
+                                                       int take_snapshot, int have_snapshot,
+                                                       double* __restrict__ partials) {
+    diag_partials<R>(D, b, snap, take_snapshot, have_snapshot, partials, blockIdx.x, gridDim.x);
+}
+
+// One lattice of a batched diagnostics pass (lbm_batch_diagnostics).
+struct DiagJob {
+    const InstDesc* D;
+    double* snap;
+    double* partials;
+    const unsigned int* status;
+    int b, have;
+};
+
+// Every lattice of one storage precision at once: blockIdx.y picks the job.
+template <typename R>
+__global__ void __launch_bounds__(kDiagThreads) k_diag_batch(const DiagJob* __restrict__ jobs, int take_snapshot) {
+    const DiagJob j = jobs[blockIdx.y];
+    diag_partials<R>(j.D, j.b, j.snap, take_snapshot, j.have, j.partials, blockIdx.x, gridDim.x);
 }
 
 __global__ void k_diag_final(const double* __restrict__ partials, int nblocks, double* __restrict__ out) {
@@ -1786,6 +1875,19 @@ __global__ void k_diag_final(const double* __restrict__ partials, int nblocks, d
     double v = 0.0;
     for (int k = 0; k < nblocks; ++k) v = (s == 8) ? fmax(v, partials[k * kDiagSlots + s]) : v + partials[k * kDiagSlots + s];
     out[s] = v;
+}
+
+// Block b finishes job b: its kDiagSlots sums, then its status word, into
+// out[b][kDiagSlots + 1], in the order k_diag_final uses.
+__global__ void k_diag_final_batch(const DiagJob* __restrict__ jobs, int nblocks, double* __restrict__ out) {
+    const DiagJob j = jobs[blockIdx.x];
+    const int s = threadIdx.x;
+    double* o = out + (size_t)blockIdx.x * (kDiagSlots + 1);
+    if (s == kDiagSlots) o[s] = (double)*j.status;
+    if (s >= kDiagSlots) return;
+    double v = 0.0;
+    for (int k = 0; k < nblocks; ++k) v = (s == 8) ? fmax(v, j.partials[k * kDiagSlots + s]) : v + j.partials[k * kDiagSlots + s];
+    o[s] = v;
 }
 
 // ------------------------------------------------------------------------
@@ -1965,7 +2067,7 @@ void convert_params(const Params<A>& a, Params<B>& b) {
     CP(rho0); CP(T0); CP(E0); CP(Cv); CP(inv_Cv); CP(Rg); CP(eos_a); CP(eos_b); CP(p0); CP(rho0E0_p0);
     CP(rho0Cp0); CP(mu0); CP(inv_T0); CP(visc_S); CP(lam_fac); CP(tj_fac); CP(e_fac); CP(alpha1);
     CP(beta1); CP(alpha2); CP(beta2); CP(kk); CP(hh); CP(bb); CP(gamma1); CP(gamma2); CP(cR11);
-    CP(cR17); CP(cR18); CP(cR71); CP(cR77); CP(cR81); CP(cR88); CP(Fx); CP(Fy); CP(cs_b0);
+    CP(cR17); CP(cR18); CP(cR71); CP(cR77); CP(cR81); CP(cR88); CP(Fx); CP(Fy); CP(cs_b0); CP(dither);
 #undef CP
     b.eos = a.eos;
     b.visc = a.visc;
@@ -1998,6 +2100,8 @@ struct lbm_ctx {
     int n_work = 0, bx = 128, by = 0, pair = 0;
     bool tile_set = false;  // launch shape chosen by lbm_set_tile, kept in batches
     int mc = 0;             // model class of the fused kernel (lbm::MODEL_*), set with the EOS
+    int round_mode = LBM_ROUND_STOCHASTIC;  // rounding of FP32 stores (lbm_set_rounding)
+    int device = 0;         // device current at lbm_create, which holds the workspace
     BWork* d_bwork = nullptr;
     int n_bwork = 0;
     long steps = 0;
@@ -2039,6 +2143,9 @@ struct lbm_batch {
     int graph_steps = 0;
     cudaGraphExec_t graph = nullptr;
     long long* d_counter = nullptr;  // batch step counter, advanced on the device
+    DiagJob* d_jobs = nullptr;       // lbm_batch_diagnostics: one job per member, FP32 members first
+    double* d_diag_out = nullptr;    // [member][kDiagSlots + 1] sums and status word
+    std::vector<int> diag_order;     // members in job order
 };
 
 namespace {
@@ -2450,10 +2557,7 @@ lbm_status check_launch() {
     return LBM_OK;
 }
 
-lbm_status read_status(lbm_ctx* c) {
-    unsigned int st = 0;
-    CUDA_TRY(cudaMemcpyAsync(&st, c->d_status, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
-    CUDA_TRY(cudaStreamSynchronize(c->stream));
+lbm_status status_bits(lbm_ctx* c, unsigned int st) {
     if (st & 4u) {
         c->sticky = LBM_ECUDA;
         return fail(LBM_ECUDA, "dynamic shared memory of the fused kernel is not 128-byte aligned");
@@ -2467,6 +2571,13 @@ lbm_status read_status(lbm_ctx* c) {
         return fail(LBM_EUNSTABLE, "non-finite density or temperature detected");
     }
     return LBM_OK;
+}
+
+lbm_status read_status(lbm_ctx* c) {
+    unsigned int st = 0;
+    CUDA_TRY(cudaMemcpyAsync(&st, c->d_status, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return status_bits(c, st);
 }
 
 bool is_fp32(const lbm_ctx* c) { return c->cfg.precision == LBM_FP32_DEV; }
@@ -2494,8 +2605,11 @@ lbm_status lbm_create(const lbm_config* cfg, void* workspace, size_t workspace_b
     lbm_status st = validate(cfg);
     if (st != LBM_OK) return st;
     if ((st = configure_kernels()) != LBM_OK) return st;
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
     lbm_ctx* c = new lbm_ctx();
     c->cfg = *cfg;
+    c->device = dev;
     c->stream = (cudaStream_t)cuda_stream;
     c->L = layout_for(*cfg);
     if (workspace) {
@@ -2663,6 +2777,7 @@ lbm_status lbm_set_eos(lbm_ctx* c, int kind, const double* params, int np) {
     P.Fx = k.force[0];
     P.Fy = k.force[1];
     P.cs_b0 = 1.0 - b * r0;
+    P.dither = c->round_mode == LBM_ROUND_NEAREST ? 0.0 : 1.0;
     P.eos = kind;
     P.visc = k.visc_law;
     P.force_mode = k.force_mode;
@@ -2719,6 +2834,61 @@ lbm_status lbm_set_eos(lbm_ctx* c, int kind, const double* params, int np) {
 lbm_status lbm_derived(const lbm_ctx* c, double* out8) {
     if (!c || !out8 || !c->eos_set) return fail(LBM_EINVAL, "context not initialised");
     memcpy(out8, c->derived, sizeof(c->derived));
+    return LBM_OK;
+}
+
+lbm_status lbm_wait_selftest(lbm_ctx* c, long long limit_cycles) {
+    if (!c || !c->eos_set) return fail(LBM_EINVAL, "context not initialised");
+    if (limit_cycles < 0 || limit_cycles > (1LL << 32)) return fail(LBM_EINVAL, "limit_cycles must lie in [0, 2^32]");
+    k_wait_selftest<<<1, 32, 0, c->stream>>>(c->d_status, limit_cycles);
+    lbm_status st = check_launch();
+    if (st != LBM_OK) return st;
+    return read_status(c);
+}
+
+lbm_status lbm_set_rounding(lbm_ctx* c, int mode) {
+    if (!c) return fail(LBM_EINVAL, "null ctx");
+    if (mode != LBM_ROUND_STOCHASTIC && mode != LBM_ROUND_NEAREST) return fail(LBM_EINVAL, "bad rounding mode");
+    c->round_mode = mode;
+    const double d = mode == LBM_ROUND_NEAREST ? 0.0 : 1.0;
+    c->h.pd.dither = d;
+    c->h.pf.dither = (float)d;
+    if (c->eos_set)
+        CUDA_TRY(cudaMemcpyAsync(c->d_desc, &c->h, sizeof(InstDesc), cudaMemcpyHostToDevice, c->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_copy_state(lbm_ctx* d, const lbm_ctx* s) {
+    if (!d || !s || !d->eos_set || !s->eos_set) return fail(LBM_EINVAL, "contexts not initialised");
+    if (d == s) return LBM_OK;
+    lbm_config a = d->cfg, b = s->cfg;
+    a.precision = b.precision = 0;
+    for (int k = 0; k < 4; ++k) a.wall[k].reserved = b.wall[k].reserved = 0;
+    if (memcmp(&a, &b, sizeof(a)) != 0) return fail(LBM_EINVAL, "lbm_copy_state needs the same problem in both contexts");
+    if (memcmp(d->f_rest, s->f_rest, sizeof(d->f_rest)) != 0 || memcmp(d->g_rest, s->g_rest, sizeof(d->g_rest)) != 0 ||
+        d->h.pd.eos != s->h.pd.eos || d->h.pd.eos_a != s->h.pd.eos_a || d->h.pd.eos_b != s->h.pd.eos_b)
+        return fail(LBM_EINVAL, "lbm_copy_state needs the same EOS in both contexts");
+    if (s->sticky != LBM_OK) return fail(s->sticky, "source context is unstable");
+    CUDA_TRY(cudaStreamSynchronize(s->stream));
+    const int nx = s->cfg.nx, ny = s->cfg.ny;
+    const long long nn = (long long)nx * ny;
+    const int sb = cur_buf(s), db = (int)(s->steps & 1);
+    const bool sf = is_fp32(s), df = is_fp32(d);
+    void* sp = s->h.buf[sb];
+    void* dp = d->h.buf[db];
+    const int grid = grid_for(18 * nn);
+    if (sf && df) k_copy_state<float, float><<<grid, 256, 0, d->stream>>>((const float*)sp, s->L.plane, s->L.pitch, (float*)dp, d->L.plane, d->L.pitch, nx, ny);
+    else if (sf) k_copy_state<float, double><<<grid, 256, 0, d->stream>>>((const float*)sp, s->L.plane, s->L.pitch, (double*)dp, d->L.plane, d->L.pitch, nx, ny);
+    else if (df) k_copy_state<double, float><<<grid, 256, 0, d->stream>>>((const double*)sp, s->L.plane, s->L.pitch, (float*)dp, d->L.plane, d->L.pitch, nx, ny);
+    else k_copy_state<double, double><<<grid, 256, 0, d->stream>>>((const double*)sp, s->L.plane, s->L.pitch, (double*)dp, d->L.plane, d->L.pitch, nx, ny);
+    lbm_status st = check_launch();
+    if (st != LBM_OK) return st;
+    if (s->have_snap) CUDA_TRY(cudaMemcpyAsync(d->d_snap, s->d_snap, 3 * nn * sizeof(double), cudaMemcpyDeviceToDevice, d->stream));
+    CUDA_TRY(cudaMemsetAsync(d->d_status, 0, 256, d->stream));
+    CUDA_TRY(cudaStreamSynchronize(d->stream));
+    d->steps = s->steps;
+    d->have_snap = s->have_snap;
+    d->sticky = LBM_OK;
     return LBM_OK;
 }
 
@@ -2882,19 +3052,9 @@ lbm_status lbm_nusselt(lbm_ctx* c, int wall, double* nu) {
     return read_status(c);
 }
 
-lbm_status lbm_diagnostics(lbm_ctx* c, int snapshot, double* out8) {
-    if (!c || !c->eos_set || !out8) return fail(LBM_EINVAL, "bad arguments");
-    const int have = c->have_snap ? 1 : 0;
-    if (is_fp32(c))
-        k_diag<float><<<kDiagBlocks, kDiagThreads, 0, c->stream>>>(c->d_desc, cur_buf(c), c->d_snap, snapshot, have, c->d_partials);
-    else
-        k_diag<double><<<kDiagBlocks, kDiagThreads, 0, c->stream>>>(c->d_desc, cur_buf(c), c->d_snap, snapshot, have, c->d_partials);
-    k_diag_final<<<1, 32, 0, c->stream>>>(c->d_partials, kDiagBlocks, c->d_diag);
-    lbm_status st = check_launch();
-    if (st != LBM_OK) return st;
-    double acc[kDiagSlots];
-    CUDA_TRY(cudaMemcpyAsync(acc, c->d_diag, sizeof(acc), cudaMemcpyDeviceToHost, c->stream));
-    CUDA_TRY(cudaStreamSynchronize(c->stream));
+// The eight outputs of lbm_diagnostics from the FP64 sums of k_diag_final;
+// records the new snapshot and turns the context sticky on non-finite nodes.
+static lbm_status diag_outputs(lbm_ctx* c, const double* acc, int snapshot, int have, double* out8) {
     const double nn = (double)c->cfg.nx * c->cfg.ny;
     const Params<double>& P = c->h.pd;
     out8[0] = nn * P.rho0 + acc[0];
@@ -2916,6 +3076,24 @@ lbm_status lbm_diagnostics(lbm_ctx* c, int snapshot, double* out8) {
         c->sticky = LBM_EUNSTABLE;
         return fail(LBM_EUNSTABLE, "non-finite nodes in the state");
     }
+    return LBM_OK;
+}
+
+lbm_status lbm_diagnostics(lbm_ctx* c, int snapshot, double* out8) {
+    if (!c || !c->eos_set || !out8) return fail(LBM_EINVAL, "bad arguments");
+    const int have = c->have_snap ? 1 : 0;
+    if (is_fp32(c))
+        k_diag<float><<<kDiagBlocks, kDiagThreads, 0, c->stream>>>(c->d_desc, cur_buf(c), c->d_snap, snapshot, have, c->d_partials);
+    else
+        k_diag<double><<<kDiagBlocks, kDiagThreads, 0, c->stream>>>(c->d_desc, cur_buf(c), c->d_snap, snapshot, have, c->d_partials);
+    k_diag_final<<<1, 32, 0, c->stream>>>(c->d_partials, kDiagBlocks, c->d_diag);
+    lbm_status st = check_launch();
+    if (st != LBM_OK) return st;
+    double acc[kDiagSlots];
+    CUDA_TRY(cudaMemcpyAsync(acc, c->d_diag, sizeof(acc), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    st = diag_outputs(c, acc, snapshot, have, out8);
+    if (st != LBM_OK) return st;
     return read_status(c);
 }
 
@@ -2929,10 +3107,15 @@ lbm_status lbm_diagnostics(lbm_ctx* c, int snapshot, double* out8) {
 static std::mutex g_static_mu;
 static double* g_static_addr[64] = {nullptr};
 
-static lbm_status static_scratch(double** out) {
+static lbm_status static_scratch(const lbm_ctx* c, double** out) {
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return fail(LBM_EINVAL, "device index out of range");
+    // the symbol address is per device: a kernel on the context's stream
+    // must get the address on the context's device
+    if (dev != c->device)
+        return fail(LBM_EINVAL, "the current device (" + std::to_string(dev) + ") is not the context's device (" +
+                                    std::to_string(c->device) + "); make the context's device current");
     std::lock_guard<std::mutex> lock(g_static_mu);
     if (!g_static_addr[dev]) {
         void* p = nullptr;
@@ -2954,7 +3137,7 @@ lbm_status lbm_conserved_sums_static(const lbm_ctx* c, double* out4) {
                                     std::to_string((long long)kStaticBlocks * kStaticNodesPerBlock) +
                                     " nodes; use lbm_diagnostics for larger lattices");
     double* scratch = nullptr;
-    lbm_status st = static_scratch(&scratch);
+    lbm_status st = static_scratch(c, &scratch);
     if (st != LBM_OK) return st;
     // every slot the final pass reads is written first, so nothing needs clearing
     if (is_fp32(c))
@@ -3166,10 +3349,57 @@ lbm_status lbm_batch_step_profiled(lbm_batch* b, long nsteps, double* ms_collide
     return LBM_OK;
 }
 
+lbm_status lbm_batch_diagnostics(lbm_batch* b, int snapshot, double* out8n, int* member_status) {
+    if (!b || !out8n) return fail(LBM_EINVAL, "bad batch diagnostics arguments");
+    const int n = (int)b->ctxs.size();
+    if (!b->d_jobs) {
+        if (cudaMalloc(&b->d_jobs, n * sizeof(DiagJob)) != cudaSuccess ||
+            cudaMalloc(&b->d_diag_out, (size_t)n * (kDiagSlots + 1) * sizeof(double)) != cudaSuccess)
+            return fail(LBM_ENOMEM, "cudaMalloc batch diagnostics");
+        for (int pr = 1; pr >= 0; --pr)
+            for (int i = 0; i < n; ++i)
+                if ((is_fp32(b->ctxs[i]) ? 1 : 0) == pr) b->diag_order.push_back(i);
+    }
+    std::vector<DiagJob> jobs(n);
+    std::vector<int> have(n);
+    int n32 = 0;
+    for (int k = 0; k < n; ++k) {
+        lbm_ctx* c = b->ctxs[b->diag_order[k]];
+        have[k] = c->have_snap ? 1 : 0;
+        jobs[k] = DiagJob{c->d_desc, c->d_snap, c->d_partials, c->d_status, cur_buf(c), have[k]};
+        n32 += is_fp32(c) ? 1 : 0;
+    }
+    CUDA_TRY(cudaMemcpyAsync(b->d_jobs, jobs.data(), n * sizeof(DiagJob), cudaMemcpyHostToDevice, b->stream));
+    if (n32) k_diag_batch<float><<<dim3(kDiagBlocks, n32), kDiagThreads, 0, b->stream>>>(b->d_jobs, snapshot);
+    if (n > n32)
+        k_diag_batch<double><<<dim3(kDiagBlocks, n - n32), kDiagThreads, 0, b->stream>>>(b->d_jobs + n32, snapshot);
+    k_diag_final_batch<<<n, 32, 0, b->stream>>>(b->d_jobs, kDiagBlocks, b->d_diag_out);
+    lbm_status st = check_launch();
+    if (st != LBM_OK) return st;
+    std::vector<double> acc((size_t)n * (kDiagSlots + 1));
+    CUDA_TRY(cudaMemcpyAsync(acc.data(), b->d_diag_out, acc.size() * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    for (int k = 0; k < n; ++k) {
+        const int i = b->diag_order[k];
+        lbm_ctx* c = b->ctxs[i];
+        const double* a = acc.data() + (size_t)k * (kDiagSlots + 1);
+        lbm_status ms = c->sticky;
+        if (ms == LBM_OK) ms = diag_outputs(c, a, snapshot, have[k], out8n + (size_t)i * 8);
+        else {
+            for (int q = 0; q < 8; ++q) out8n[(size_t)i * 8 + q] = std::nan("");
+        }
+        if (ms == LBM_OK) ms = status_bits(c, (unsigned int)a[kDiagSlots]);
+        if (member_status) member_status[i] = ms;
+    }
+    return LBM_OK;
+}
+
 lbm_status lbm_batch_destroy(lbm_batch* b) {
     if (!b) return LBM_OK;
     if (b->stream) cudaStreamSynchronize(b->stream);
     else cudaDeviceSynchronize();
+    if (b->d_jobs) cudaFree(b->d_jobs);
+    if (b->d_diag_out) cudaFree(b->d_diag_out);
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->d_counter) cudaFree(b->d_counter);
     if (b->d_descs) cudaFree(b->d_descs);

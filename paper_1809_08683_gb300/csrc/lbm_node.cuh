@@ -65,6 +65,7 @@ struct Params {
     R cR11, cR17, cR18, cR71, cR77, cR81, cR88;
     R Fx, Fy;
     R cs_b0;  // 1 - b rho0 (cubic EOS)
+    R dither; // FP32 storage: 1 rounds the stored deviations stochastically, 0 to nearest
     int eos, visc, force_mode, corrections;
 };
 

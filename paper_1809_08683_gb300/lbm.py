@@ -16,7 +16,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "csrc", "lbm_gb300.cu")
-_DEPS = [_SRC, os.path.join(_HERE, "csrc", "lbm_node.cuh"),
+_DEPS = [_SRC, os.path.join(_HERE, "csrc", "lbm_node.cuh"), os.path.join(_HERE, "csrc", "lbm_f2.cuh"),
          os.path.join(os.path.dirname(_HERE), "include", "lbm.h")]
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "liblbm_gb300.so")
@@ -25,6 +25,7 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a",
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT = 0, -1, -2, -3, -4, -5
 FP64, FP32_DEV = 0, 1
+ROUND_STOCHASTIC, ROUND_NEAREST = 0, 1
 
 _lock = threading.Lock()
 _lib = None
@@ -72,7 +73,8 @@ EXPORTS = ("lbm_workspace_bytes", "lbm_create", "lbm_set_eos", "lbm_step", "lbm_
            "lbm_macros_device", "lbm_nusselt", "lbm_diagnostics", "lbm_get_state", "lbm_set_state",
            "lbm_init_macros", "lbm_derived", "lbm_set_tile", "lbm_get_tile", "lbm_step_count", "lbm_destroy",
            "lbm_last_error", "lbm_batch_create", "lbm_batch_step", "lbm_batch_step_profiled",
-           "lbm_batch_destroy", "lbm_conserved_sums_static")
+           "lbm_batch_destroy", "lbm_conserved_sums_static", "lbm_set_rounding", "lbm_copy_state",
+           "lbm_wait_selftest", "lbm_batch_diagnostics")
 
 
 def load(path: str | None = None):
@@ -111,6 +113,10 @@ def load(path: str | None = None):
         L.lbm_batch_step_profiled.argtypes = [vp, C.c_long, dp, dp]
         L.lbm_batch_destroy.argtypes = [vp]
         L.lbm_conserved_sums_static.argtypes = [vp, vp]
+        L.lbm_set_rounding.argtypes = [vp, i]
+        L.lbm_copy_state.argtypes = [vp, vp]
+        L.lbm_wait_selftest.argtypes = [vp, C.c_longlong]
+        L.lbm_batch_diagnostics.argtypes = [vp, i, dp, P(C.c_int)]
         _lib = L
         return L
 
@@ -269,6 +275,15 @@ class Lattice:
         _check(self.L, self.L.lbm_get_tile(self.h, C.byref(bx), C.byref(by), C.byref(pr)))
         return bx.value, by.value, pr.value
 
+    def set_rounding(self, mode: int):
+        """ROUND_STOCHASTIC (default) or ROUND_NEAREST for FP32 stores."""
+        _check(self.L, self.L.lbm_set_rounding(self.h, int(mode)))
+
+    def copy_state_from(self, other: "Lattice"):
+        """Take the state, step count and residual snapshot of another lattice
+        of the same problem, converting the storage precision."""
+        _check(self.L, self.L.lbm_copy_state(self.h, other.h))
+
     def conserved_sums_static(self, out):
         """Total mass, x and y momentum and sum of g into the device tensor
         ``out`` (4 doubles) without any allocation; asynchronous."""
@@ -298,6 +313,17 @@ class Batch:
         a, b = C.c_double(), C.c_double()
         _check(self.L, self.L.lbm_batch_step_profiled(self.h, int(n), C.byref(a), C.byref(b)))
         return a.value, b.value
+
+    def diagnostics(self, snapshot: bool = False):
+        """lbm_diagnostics of every member in one pass: a list of (dict,
+        status) in member order; status is LBM_OK or the member's sticky
+        error."""
+        n = len(self.lattices)
+        a = np.empty(n * 8)
+        st = (C.c_int * n)()
+        _check(self.L, self.L.lbm_batch_diagnostics(self.h, int(bool(snapshot)), _ptr(a), st))
+        keys = ("mass", "energy", "pstar", "residual", "nonfinite", "umax", "Tmean", "steps")
+        return [(dict(zip(keys, a[8 * k:8 * k + 8].tolist())), int(st[k])) for k in range(n)]
 
     def close(self):
         if getattr(self, "h", None):

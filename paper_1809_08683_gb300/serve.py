@@ -3,13 +3,23 @@
 Requests (a cavity or channel configuration, a residual target and a step
 cap) arrive over time.  The server keeps every admitted lattice resident in
 HBM and advances all resident lattices together: one batched fused launch
-and one batched wall-pass launch per time step, replayed from a CUDA graph in
-chunks of ``chunk`` steps.  After each chunk it evaluates the FP64 residual of
-every resident lattice (relative change of u and T over the chunk), retires
-converged or capped solves, and admits newly arrived requests while slots and
-device memory allow.  A request that arrives while others run joins at the
-next chunk boundary.  Per-node arithmetic does not depend on the batch, so a
-request's result is bitwise the same alone and in any mix.
+per launch group and one batched wall-pass launch per time step, replayed
+from a CUDA graph in chunks of ``chunk`` steps.  After each chunk one
+batched diagnostics pass (one synchronisation) gives the FP64 residual of
+every resident lattice (relative change of u and T over the chunk); the
+server retires converged, capped or unstable solves and admits arrived
+requests while slots and device memory allow, first fit in arrival order,
+so a small request is not held back behind a large one that does not fit
+yet.  The batch is rebuilt only when the resident set changes.
+
+Precision: a request whose configuration asks for FP32 deviation storage is
+stepped in FP32 until its residual falls below ``fp32_floor`` (stochastic
+rounding keeps FP32 residuals from falling much below 1e-6); if its target
+is tighter, the solve is finished in FP64 from the FP32 state
+(lbm_copy_state), so that every result meets its stated target.  A
+request's result is bitwise the same alone and in any mix: per-node
+arithmetic does not depend on the batch, residual checks fall on the same
+step counts, and stochastic rounding draws from (node, absolute step) only.
 """
 from __future__ import annotations
 
@@ -33,6 +43,7 @@ class Request:
     steps: int = 0
     converged: bool = False
     status: str = "pending"
+    switched_at: int | None = None   # step count at which an FP32 solve moved to FP64
     result: dict = field(default_factory=dict)
 
     @property
@@ -56,9 +67,63 @@ def summarise(lat, req):
     return out
 
 
+def _fp64(cfg):
+    c = dict(cfg)
+    c["precision"] = lbm.FP64
+    return c
+
+
+class _Timer:
+    """Device time between start() and stop() on the serving stream (CUDA
+    events); wall-clock time when the stream is not a CUDA stream."""
+
+    def __init__(self, stream):
+        import torch
+        self.cuda = isinstance(stream, torch.cuda.Stream)
+        self.stream = stream
+        if self.cuda:
+            self.e0 = torch.cuda.Event(enable_timing=True)
+            self.e1 = torch.cuda.Event(enable_timing=True)
+
+    def start(self):
+        if self.cuda:
+            self.e0.record(self.stream)
+        else:
+            self.t0 = time.perf_counter()
+
+    def stop(self):
+        if self.cuda:
+            self.e1.record(self.stream)
+        else:
+            self.t1 = time.perf_counter()
+
+    def ms(self):
+        if self.cuda:
+            self.e1.synchronize()
+            return self.e0.elapsed_time(self.e1)
+        return (self.t1 - self.t0) * 1e3
+
+
+class _Slot:
+    __slots__ = ("req", "lat", "bytes")
+
+    def __init__(self, req, lat, nbytes):
+        self.req, self.lat, self.bytes = req, lat, nbytes
+
+
 class Server:
+    """max_slots: resident lattices at most.  mem_fraction: share of the
+    device memory free at construction that resident lattices may take; the
+    memory free at each admission (minus the rest of the device as
+    headroom) is checked as well, so memory that other work takes or frees
+    later is seen.  fp32_floor: the residual below which FP32 storage is not
+    trusted to converge; None keeps FP32 to the end (targets must then be
+    above the floor).  starvation_s: a request that has waited this long
+    stops later arrivals from overtaking it (None: never)."""
+
     def __init__(self, max_slots: int = 64, mem_fraction: float = 0.85, chunk: int = 1000,
-                 graph_steps: int = 100, stream=None, tile_fn=None, keep_fields: bool = False):
+                 graph_steps: int = 100, stream=None, tile_fn=None, keep_fields: bool = False,
+                 fp32_floor: float | None = 3e-6, starvation_s: float | None = None):
         import torch
         self.torch = torch
         self.max_slots = max_slots
@@ -68,75 +133,131 @@ class Server:
         self.stream = stream if stream is not None else torch.cuda.Stream()
         self.tile_fn = tile_fn
         self.keep_fields = keep_fields
+        self.fp32_floor = fp32_floor
+        self.starvation_s = starvation_s
         free, total = torch.cuda.mem_get_info()
+        self.total = total
         self.budget = int(free * mem_fraction)
+        self.headroom = int(total * (1.0 - mem_fraction))
         self.in_use = 0
         self.node_steps = 0
+        self.gpu_ms = 0.0          # device time of the stepping, summed over chunks
+        self.chunks = 0
+        self.rebuilds = 0
         self.log = []
 
-    def _fits(self, req):
-        return self.in_use + lbm.workspace_bytes(req.cfg) <= self.budget
+    # -- device memory ----------------------------------------------------
+    def _live_free(self):
+        """Device memory free now, counting what the caching allocator holds
+        unused as free."""
+        free, _ = self.torch.cuda.mem_get_info()
+        try:
+            cached = self.torch.cuda.memory_reserved() - self.torch.cuda.memory_allocated()
+        except Exception:
+            cached = 0
+        return free + max(0, cached)
 
+    def _fits(self, nbytes):
+        return (self.in_use + nbytes <= self.budget) and (nbytes <= self._live_free() - self.headroom)
+
+    def _new_lattice(self, cfg):
+        if isinstance(self.stream, self.torch.cuda.Stream):
+            # the workspace belongs to the serving stream, so the caching
+            # allocator reuses it only in that stream's order
+            with self.torch.cuda.stream(self.stream):
+                lat = lbm.Lattice(cfg, stream=self.stream)
+        else:
+            lat = lbm.Lattice(cfg, stream=self.stream)
+        if self.tile_fn is not None:
+            lat.set_tile(*self.tile_fn(cfg))
+        return lat
+
+    # -- the loop ----------------------------------------------------------
     def run(self, requests, realtime: bool = True):
         """Serve the requests; arrival times are honoured against the wall
         clock when realtime is True, otherwise every request is available at
         once.  Returns the list of requests with their results filled."""
+        torch = self.torch
         pending = sorted(requests, key=lambda r: r.arrival)
-        resident = []          # (request, lattice)
+        resident: list[_Slot] = []
         batch = None
         dirty = True
+        timer = _Timer(self.stream)
         t0 = time.perf_counter()
         while pending or resident:
             now = time.perf_counter() - t0
-            while (pending and (not realtime or pending[0].arrival <= now)
-                   and len(resident) < self.max_slots and self._fits(pending[0])):
-                r = pending.pop(0)
-                lat = lbm.Lattice(r.cfg, stream=self.stream)
-                if self.tile_fn is not None:
-                    lat.set_tile(*self.tile_fn(r.cfg))
+            # admission: first fit in arrival order
+            i = 0
+            while i < len(pending) and len(resident) < self.max_slots:
+                r = pending[i]
+                if realtime and r.arrival > now:
+                    break
+                nbytes = lbm.workspace_bytes(r.cfg)
+                if not self._fits(nbytes):
+                    if self.starvation_s is not None and now - r.arrival > self.starvation_s:
+                        break
+                    i += 1
+                    continue
+                pending.pop(i)
+                lat = self._new_lattice(r.cfg)
                 lat.diagnostics(snapshot=True)
-                self.in_use += lbm.workspace_bytes(r.cfg)
+                self.in_use += nbytes
                 r.admitted = time.perf_counter() - t0
                 r.status = "running"
-                resident.append((r, lat))
+                resident.append(_Slot(r, lat, nbytes))
                 dirty = True
             if not resident:
-                if pending:
-                    if realtime:
-                        time.sleep(max(0.0, min(0.01, pending[0].arrival - now)))
-                    else:
-                        raise RuntimeError(f"request {pending[0].rid} does not fit the device budget")
+                future = [r for r in pending if realtime and r.arrival > now]
+                if not future:
+                    # everything has arrived, nothing is resident, nothing fits
+                    raise RuntimeError(f"request {pending[0].rid} does not fit the device budget")
+                time.sleep(max(0.0, min(0.01, future[0].arrival - now)))
                 continue
             if dirty:
                 if batch is not None:
                     batch.close()
-                batch = lbm.Batch([lat for _, lat in resident], graph_steps=self.graph_steps)
+                batch = lbm.Batch([s.lat for s in resident], graph_steps=self.graph_steps)
+                self.rebuilds += 1
                 dirty = False
+            timer.start()
             batch.step(self.chunk)
-            self.node_steps += self.chunk * sum(r.nodes for r, _ in resident)
+            timer.stop()
+            diags = batch.diagnostics(snapshot=True)
+            self.gpu_ms += timer.ms()
+            self.chunks += 1
+            self.node_steps += self.chunk * sum(s.req.nodes for s in resident)
             keep = []
-            for r, lat in resident:
+            for slot, (d, st) in zip(resident, diags):
+                r = slot.req
                 r.steps += self.chunk
-                try:
-                    d = lat.diagnostics(snapshot=True)
-                    r.result["residual"] = d["residual"]
-                    done = (r.steps >= r.min_steps and d["residual"] < r.tol)
-                    r.converged = done
-                    if done or r.steps >= r.max_steps:
-                        r.status = "converged" if done else "capped"
-                except lbm.LbmError as e:
+                if st != lbm.LBM_OK:
                     r.status = "unstable"
-                    r.result["error"] = str(e)
+                    r.result["error"] = f"lbm status {st}"
+                else:
+                    r.result["residual"] = d["residual"]
+                    fp32 = int(slot.lat.cfg.get("precision", 0)) == lbm.FP32_DEV
+                    target = r.tol
+                    if fp32 and self.fp32_floor is not None:
+                        target = max(r.tol, self.fp32_floor)
+                    if r.steps >= r.min_steps and d["residual"] < target:
+                        if target > r.tol and self._switch_to_fp64(slot):
+                            r.switched_at = r.steps
+                            dirty = True
+                        else:
+                            r.converged = True
+                            r.status = "converged"
+                    if r.status == "running" and r.steps >= r.max_steps:
+                        r.status = "capped"
                 if r.status == "running":
-                    keep.append((r, lat))
+                    keep.append(slot)
                     continue
                 r.finished = time.perf_counter() - t0
                 if r.status != "unstable":
-                    r.result.update(summarise(lat, r))
+                    r.result.update(summarise(slot.lat, r))
                     if self.keep_fields:
-                        r.result["fields"] = lat.macros()
-                self.in_use -= lbm.workspace_bytes(r.cfg)
-                lat.close()
+                        r.result["fields"] = slot.lat.macros()
+                self.in_use -= slot.bytes
+                slot.lat.close()
                 dirty = True
             if dirty and batch is not None:
                 batch.close()
@@ -148,10 +269,32 @@ class Server:
         self.wall = time.perf_counter() - t0
         return requests
 
+    def _switch_to_fp64(self, slot):
+        """Move a converged FP32 solve to FP64 storage (state, step count and
+        residual snapshot copied); False when the FP64 lattice does not fit
+        now (the solve then stays in FP32 and retries after the next chunk)."""
+        cfg = _fp64(slot.lat.cfg)
+        nbytes = lbm.workspace_bytes(cfg)
+        if not self._fits(nbytes):
+            return False
+        lat = self._new_lattice(cfg)
+        lat.copy_state_from(slot.lat)
+        slot.lat.close()
+        self.in_use += nbytes - slot.bytes
+        slot.lat, slot.bytes = lat, nbytes
+        return True
 
-def solve_sequential(req: Request, chunk: int = 1000, keep_fields: bool = False):
-    """Plain per-request solve: FP64 lattice alone, per-step launches, the
-    same residual schedule.  The baseline the batched server is compared to."""
+    @property
+    def host_overhead(self):
+        """Share of the wall time the device spent not stepping: scheduling,
+        diagnostics, admissions, retirements and batch rebuilds."""
+        return max(0.0, 1.0 - self.gpu_ms * 1e-3 / self.wall) if getattr(self, "wall", 0) else None
+
+
+def solve_sequential(req: Request, chunk: int = 1000, keep_fields: bool = False, fp32_floor: float | None = 3e-6):
+    """Plain per-request solve: the lattice alone, per-step launches, the
+    same residual schedule (and the same FP32-to-FP64 finish for targets
+    below fp32_floor).  The baseline the batched server is compared to."""
     lat = lbm.Lattice(req.cfg)
     lat.diagnostics(snapshot=True)
     t0 = time.perf_counter()
@@ -160,7 +303,16 @@ def solve_sequential(req: Request, chunk: int = 1000, keep_fields: bool = False)
         req.steps += chunk
         d = lat.diagnostics(snapshot=True)
         req.result["residual"] = d["residual"]
-        if req.steps >= req.min_steps and d["residual"] < req.tol:
+        fp32 = int(lat.cfg.get("precision", 0)) == lbm.FP32_DEV
+        target = max(req.tol, fp32_floor) if (fp32 and fp32_floor is not None) else req.tol
+        if req.steps >= req.min_steps and d["residual"] < target:
+            if target > req.tol:
+                lat64 = lbm.Lattice(_fp64(lat.cfg))
+                lat64.copy_state_from(lat)
+                lat.close()
+                lat = lat64
+                req.switched_at = req.steps
+                continue
             req.converged = True
             req.status = "converged"
             break

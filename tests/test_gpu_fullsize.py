@@ -47,4 +47,8 @@ def test_batched_sweep_sampled_members_match_oracle(orc, lbm):
                "uy": np.abs(mg["uy"] - mo["uy"]).max() / umax,
                "T": np.abs(mg["T"] - mo["T"]).max() / np.abs(mo["T"]).max()}
         assert all(v < TOL32 for v in err.values()), (sides[i], err)
+        # deviations from the rest state, each against its own size
+        dev = {"rho_dev": np.abs(mg["rho"] - mo["rho"]).max() / np.abs(mo["rho"] - 1.0).max(),
+               "T_dev": np.abs(mg["T"] - mo["T"]).max() / np.abs(mo["T"] - 1.0).max()}
+        assert all(v < 1e-3 for v in dev.values()), (sides[i], dev)
     batch.close()

@@ -263,3 +263,51 @@ def test_relaxation_rate_rules(orc):
     assert abs(d["Cp"] / 3 * (1 / sig[3] - 0.5) - lam) < 1e-15
     assert abs((1 / sig[3] - 0.5) * (1 / sig[1] - 0.5) - 0.25) < 1e-14
     assert sig[0] == 1 and sig[1] == sig[2] == sig[7] == sig[8] and sig[3] == sig[4] == sig[5] == sig[6]
+
+
+def _quadratic(nx, ny, c):
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    a, b, cy, d, e, f = c
+    phi = a + b * x + cy * y + d * x * x + e * x * y + f * y * y
+    return phi, b + 2 * d * x + e * y, cy + e * x + 2 * f * y
+
+
+@pytest.mark.parametrize("nx,ny", [(9, 7), (5, 5), (13, 4)])
+def test_gradient_stencil_exact_on_quadratics(orc, nx, ny):
+    # Step 2 of the oracle (the stencil the paper leaves to cited work,
+    # reading R3): the isotropic interior stencil 3 sum_i w_i e_i phi(x + e_i),
+    # the one-sided second-order difference along a wall normal and the
+    # central one along the wall are all exact for a quadratic field, at
+    # interior nodes, on every wall and in the corners.  The x and y
+    # coefficients differ, so a swapped axis, a wrong sign of the inward
+    # normal, a dropped diagonal weight or a first-order wall formula fails.
+    o = orc.Oracle(W.cavity(N=8, Ra=1e3, eps=0.5) | {"nx": nx, "ny": ny})
+    rng = np.random.default_rng(nx * 31 + ny)
+    for _ in range(3):
+        c = rng.uniform(-1, 1, 6)
+        phi, gx_ref, gy_ref = _quadratic(nx, ny, c)
+        gx, gy = o.grad_field(phi)
+        assert np.abs(gx - gx_ref).max() < 1e-12
+        assert np.abs(gy - gy_ref).max() < 1e-12
+    # a cubic term along x is not differentiated exactly by a second-order
+    # formula: the check above is not vacuous
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    gx, _ = o.grad_field(x ** 3)
+    assert np.abs(gx - 3 * x ** 2).max() > 0.5
+    o.close()
+
+
+def test_gradient_stencil_periodic_fourier_mode(orc):
+    # On a periodic lattice the stencil applied to sin(k x) (or sin(k y))
+    # gives exactly sin(k) cos(k x): the weights 1/9 (axis) and 1/36
+    # (diagonal) sum to 1/6 per side, 3 * 2 * (1/6) = 1, times the central
+    # difference (phi(x+1) - phi(x-1)) / 2 = sin(k) cos(k x).  The wrap
+    # across the periodic edge takes part at both ends.
+    nx, ny = 12, 10
+    o = orc.Oracle(W.periodic_box(nx, ny))
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    kx, ky = 2 * np.pi * 2 / nx, 2 * np.pi / ny
+    gx, gy = o.grad_field(np.sin(kx * x) + 0.5 * np.sin(ky * y))
+    assert np.abs(gx - np.sin(kx) * np.cos(kx * x)).max() < 1e-13
+    assert np.abs(gy - 0.5 * np.sin(ky) * np.cos(ky * y)).max() < 1e-13
+    o.close()

@@ -19,22 +19,37 @@ class FakeError(RuntimeError):
 def fake_library(trace):
     """A stand-in for the lbm module: each config carries its script under
     cfg["fake"] = {"bytes": workspace bytes, "decay": residual factor per
-    1000 steps, "unstable_at": step count at which diagnostics fail}."""
+    1000 steps, "unstable_at": step count at which diagnostics fail,
+    "floor": residual below which FP32 storage does not get}.  A FP64
+    configuration takes twice the bytes of its FP32 one."""
 
     class Lattice:
         def __init__(self, cfg, stream=None):
             self.cfg, self.steps, self.closed = cfg, 0, False
-            trace["created"].append(cfg["rid"])
+            trace["created"].append((cfg["rid"], int(cfg.get("precision", 0))))
 
         def set_tile(self, *a):
             pass
 
-        def diagnostics(self, snapshot=False):
+        def copy_state_from(self, other):
+            self.steps = other.steps
+            trace["copied"].append(self.cfg["rid"])
+
+        def residual(self):
             s = self.cfg["fake"]
-            if s.get("unstable_at") is not None and self.steps >= s["unstable_at"]:
+            r = 1.0 * s["decay"] ** (self.steps / 1000.0) if self.steps else 1.0
+            if int(self.cfg.get("precision", 0)) == 1:
+                r = max(r, s.get("floor", 0.0))
+            return r
+
+        def unstable(self):
+            s = self.cfg["fake"]
+            return s.get("unstable_at") is not None and self.steps >= s["unstable_at"]
+
+        def diagnostics(self, snapshot=False):
+            if self.unstable():
                 raise FakeError("non-finite state")
-            residual = 1.0 * s["decay"] ** (self.steps / 1000.0) if self.steps else 1.0
-            return {"residual": residual, "mass": 1.0, "pstar": 1.0, "umax": 0.0, "Tmean": 1.0}
+            return {"residual": self.residual(), "mass": 1.0, "pstar": 1.0, "umax": 0.0, "Tmean": 1.0}
 
         def nusselt(self, wall):
             return 1.0
@@ -56,31 +71,44 @@ def fake_library(trace):
                 assert not l.closed
                 l.steps += n
 
+        def diagnostics(self, snapshot=False):
+            trace["diag_calls"] += 1
+            return [({}, -4) if l.unstable() else ({"residual": l.residual()}, 0) for l in self.lattices]
+
         def close(self):
             pass
 
-    return types.SimpleNamespace(Lattice=Lattice, Batch=Batch, LbmError=FakeError,
-                                 workspace_bytes=lambda cfg: cfg["fake"]["bytes"])
+    def workspace_bytes(cfg):
+        # a request made in FP32 storage takes twice its bytes once in FP64
+        b = cfg["fake"]["bytes"]
+        return 2 * b if (cfg["fake"]["fp32"] and int(cfg.get("precision", 0)) == 0) else b
+
+    return types.SimpleNamespace(Lattice=Lattice, Batch=Batch, LbmError=FakeError, LBM_OK=0, FP64=0, FP32_DEV=1,
+                                 workspace_bytes=workspace_bytes)
 
 
-def make_requests(specs):
+def make_requests(specs, precision=0, tol=1.5e-3, floor=0.0):
     reqs = []
     for rid, (arrival, bytes_, decay, unstable_at, max_steps) in enumerate(specs):
-        cfg = W.couette(nx=4, ny=8)
+        cfg = W.couette(nx=4, ny=8, precision=precision)
         cfg["rid"] = rid
-        cfg["fake"] = {"bytes": bytes_, "decay": decay, "unstable_at": unstable_at}
-        reqs.append(serve.Request(rid=rid, cfg=cfg, arrival=arrival, tol=1.5e-3, max_steps=max_steps))
+        cfg["fake"] = {"bytes": bytes_, "decay": decay, "unstable_at": unstable_at, "floor": floor,
+                       "fp32": precision == 1}
+        reqs.append(serve.Request(rid=rid, cfg=cfg, arrival=arrival, tol=tol, max_steps=max_steps))
     return reqs
 
 
 @pytest.fixture
 def server_factory(monkeypatch):
     import torch
-    trace = {"created": [], "batches": []}
+    trace = {"created": [], "batches": [], "copied": [], "diag_calls": 0}
     monkeypatch.setattr(serve, "lbm", fake_library(trace))
+    monkeypatch.setattr(torch.cuda, "memory_reserved", lambda *a: 0)
+    monkeypatch.setattr(torch.cuda, "memory_allocated", lambda *a: 0)
 
-    def make(free_bytes, **kw):
-        monkeypatch.setattr(torch.cuda, "mem_get_info", lambda *a: (free_bytes, free_bytes))
+    def make(free_bytes, free_fn=None, **kw):
+        monkeypatch.setattr(torch.cuda, "mem_get_info",
+                            free_fn or (lambda *a: (free_bytes, free_bytes)))
         return serve.Server(stream=object(), **kw)
 
     return make, trace
@@ -101,9 +129,11 @@ def test_outcomes_slots_and_ledger(server_factory):
     assert [r.steps for r in reqs] == [3000, 5000, 2000, 3000, 3000]
     assert all(r.finished is not None and r.admitted is not None for r in reqs)
     assert max(n for _, n, _ in srv.log) <= 2               # never more than max_slots resident
-    assert trace["created"] == [0, 1, 2, 3, 4]               # admitted in arrival order
+    assert [rid for rid, _ in trace["created"]] == [0, 1, 2, 3, 4]   # admitted in arrival order
     assert srv.in_use == 0                                    # every admission released
     assert "error" in reqs[2].result and "mass" in reqs[0].result
+    # one batched diagnostics pass per chunk, whatever the number resident
+    assert trace["diag_calls"] == len(srv.log)
 
 
 def test_memory_budget_limits_admission(server_factory):
@@ -114,6 +144,8 @@ def test_memory_budget_limits_admission(server_factory):
     srv.run(reqs, realtime=False)
     assert all(r.status == "converged" for r in reqs)
     assert max(len(b) for b in trace["batches"]) == 2
+    # the batch is rebuilt only when the resident set changes
+    assert len(trace["batches"]) == 2
     assert reqs[2].admitted >= reqs[0].finished              # the third waited for room
 
 
@@ -142,3 +174,87 @@ def test_percentiles_skip_missing_values():
     p = serve.percentiles([1.0, None, 3.0, 2.0])
     assert p["p50"] == 2.0 and abs(p["p99"] - 2.98) < 1e-12
     assert serve.percentiles([None]) == {"p50": None, "p99": None}
+
+
+def test_small_request_overtakes_one_that_does_not_fit(server_factory):
+    make, trace = server_factory
+    # a running request of 600 bytes leaves 400 of 1000; the next arrival
+    # (500 bytes) does not fit, the one after it (300 bytes) does and is
+    # admitted at once instead of waiting behind it
+    reqs = make_requests([(0.0, 600, 0.5, None, 20000), (0.0, 500, 0.1, None, 10000),
+                          (0.0, 300, 0.1, None, 10000)])
+    srv = make(1000, max_slots=8, mem_fraction=1.0, chunk=1000, graph_steps=0)
+    srv.run(reqs, realtime=False)
+    assert all(r.status == "converged" for r in reqs)
+    assert reqs[2].admitted < reqs[0].finished                # overtook request 1
+    assert reqs[1].admitted >= reqs[0].finished               # which waited for room
+    assert [rid for rid, _ in trace["created"]] == [0, 2, 1]
+
+
+def test_starvation_limit_stops_overtaking(server_factory):
+    make, trace = server_factory
+    reqs = make_requests([(0.0, 600, 0.5, None, 20000), (0.0, 500, 0.1, None, 10000),
+                          (0.0, 300, 0.1, None, 10000)])
+    srv = make(1000, max_slots=8, mem_fraction=1.0, chunk=1000, graph_steps=0, starvation_s=0.0)
+    srv.run(reqs, realtime=False)
+    assert [rid for rid, _ in trace["created"]] == [0, 1, 2]
+
+
+def test_admission_sees_memory_taken_by_others(server_factory):
+    make, trace = server_factory
+    # the ledger alone would admit both requests at once; another user of
+    # the device takes 800 of the 1000 free bytes right after the first
+    # admission and gives them back when the first request retires, so the
+    # second request waits for the live free memory, not for the ledger
+    state = {"free": 1000}
+    reqs = make_requests([(0.0, 300, 0.1, None, 10000), (0.0, 300, 0.1, None, 10000)])
+    srv = make(1000, free_fn=lambda *a: (state["free"], 1000), max_slots=8, mem_fraction=1.0, chunk=1000,
+               graph_steps=0)
+    orig_new, orig_close = serve.Server._new_lattice, serve.lbm.Lattice.close
+
+    def take_memory(self, cfg):
+        lat = orig_new(self, cfg)
+        if cfg["rid"] == 0:
+            state["free"] = 200
+        return lat
+
+    def give_back(lat):
+        orig_close(lat)
+        if lat.cfg["rid"] == 0:
+            state["free"] = 1000
+
+    serve.Server._new_lattice = take_memory
+    serve.lbm.Lattice.close = give_back
+    try:
+        srv.run(reqs, realtime=False)
+    finally:
+        serve.Server._new_lattice = orig_new
+        serve.lbm.Lattice.close = orig_close
+    assert all(r.status == "converged" for r in reqs)
+    assert trace["batches"][0] == [0]
+    assert reqs[1].admitted >= reqs[0].finished
+
+
+def test_fp32_solve_below_its_floor_finishes_in_fp64(server_factory):
+    make, trace = server_factory
+    # FP32 stalls at a residual of 1e-6; the target is 1e-8: the solve
+    # switches to FP64 storage once below the floor (3e-6) and finishes there
+    reqs = make_requests([(0.0, 100, 0.1, None, 20000), (0.0, 100, 0.1, None, 20000)],
+                         precision=1, tol=1e-8, floor=1e-6)
+    reqs[1].tol = 2e-5                       # above the floor: stays FP32
+    srv = make(10_000, max_slots=8, mem_fraction=1.0, chunk=1000, graph_steps=0, fp32_floor=3e-6)
+    srv.run(reqs, realtime=False)
+    assert [r.status for r in reqs] == ["converged", "converged"]
+    assert reqs[0].switched_at == 6000 and reqs[0].steps == 9000
+    assert reqs[1].switched_at is None and reqs[1].steps == 5000
+    assert (0, 0) in trace["created"] and (1, 0) not in trace["created"]
+    assert trace["copied"] == [0]
+    assert srv.in_use == 0
+
+
+def test_fp32_without_a_floor_caps(server_factory):
+    make, _ = server_factory
+    reqs = make_requests([(0.0, 100, 0.1, None, 20000)], precision=1, tol=1e-8, floor=1e-6)
+    srv = make(10_000, max_slots=8, mem_fraction=1.0, chunk=1000, graph_steps=0, fp32_floor=None)
+    srv.run(reqs, realtime=False)
+    assert reqs[0].status == "capped" and reqs[0].switched_at is None

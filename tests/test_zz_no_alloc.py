@@ -53,6 +53,38 @@ def test_static_sums_match_diagnostics_on_two_calls(lbm, precision):
     lat.close()
 
 
+def _check_static(lbm, lat, out):
+    st = lat.L.lbm_conserved_sums_static(lat.h, C.c_void_p(out.data_ptr()))
+    assert st == lbm.LBM_OK, lat.L.lbm_last_error()
+    lat.stream.synchronize()
+    got = out.cpu().numpy()
+    d = lat.diagnostics()
+    f, g = lat.get_state()
+    mass = d["mass"]
+    assert abs(got[0] / mass - 1) < 1e-12
+    assert abs(got[3] / d["energy"] - 1) < 1e-12
+    assert abs(got[3] - g.sum()) < 1e-12 * abs(d["energy"])
+    assert abs(got[1] - (EX[:, None, None] * f).sum()) < 1e-12 * mass
+    assert abs(got[2] - (EY[:, None, None] * f).sum()) < 1e-12 * mass
+
+
+def test_static_sums_several_blocks_then_one(lbm):
+    """A lattice of three blocks of nodes (300 x 300 > 2 x 32768), then a
+    one-block lattice right after it: the second call's final pass reads
+    only the slot its own first pass wrote, not the larger lattice's."""
+    import torch
+    big = lbm.Lattice(W.couette(nx=300, ny=300, precision=1))
+    small = lbm.Lattice(W.couette(nx=37, ny=80, precision=1))
+    out = torch.full((4,), float("nan"), dtype=torch.float64, device=big.device)
+    for _ in range(2):
+        big.step(40)
+        small.step(40)
+        _check_static(lbm, big, out)
+        _check_static(lbm, small, out)
+    big.close()
+    small.close()
+
+
 def test_static_sums_reject_lattices_beyond_capacity(lbm):
     import torch
     cfg = W.periodic_box(8193, 8192, precision=1)   # 1 node row more than 2048 x 32768 nodes
