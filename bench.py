@@ -4,20 +4,30 @@ on GB300.
 Default workload: the batched sweep of 96 heated cavities (sides 192..1024
 from Ra log-uniform in [1e3, 1e8], eps in [0.1, 0.6], ideal or cubic EOS,
 FP32 deviation storage; 39.2M nodes, 11 GB of DFs), advanced together.  One
-bench step = `--chunk` time steps of every cavity (fused collide + stream
-launch and wall-pass launch per time step).  Metric: MLUPS, one lattice-node
-update of both f and g per node per time step.
+bench step = `--chunk` time steps of every cavity.  Metric: MLUPS, one
+lattice-node update of both f and g per node per time step.
 
-Lines printed (one JSON line per run, rank 0):
-  value     device-timed MLUPS over the timed region (CUDA events, inputs
-            resident in HBM; state 11 GB >> 129 MB L2, so no flush is needed)
+Fields of the JSON line (rank 0):
+  value     device-timed MLUPS over the timed region: the batch replayed
+            from a CUDA graph of `chunk` time steps (one fused launch per
+            launch group and one wall-pass launch per time step), in the
+            launch shape the batch autotuner picked; CUDA events, inputs
+            resident in HBM, state 11 GB >> 129 MB L2 (no flush needed)
+  autotune  the batch's launch shape: default, pick, ms per step of each
+  ungraphed the same batch stepped with per-step launches and per-step
+            CUDA events, which also give the fused/wall-pass split
   e2e       same metric through the public API with host buffers: per bench
             step, equilibrium initialisation from pinned host fields (H2D),
-            the chunk of time steps, and the macroscopic fields back (D2H);
-            one untimed round first, then --e2e-steps timed rounds
+            the chunk of time steps, and the macroscopic fields back (D2H)
   roofline  the fused kernel's algorithmic bytes (18 DF reads + 18 DF writes
             per node) over its CUDA-event duration, against the measured HBM
             copy bandwidth
+  time_to_steady  the 512^2 Ra = 1e6 cavity run to residual 1e-8 (FP32, then
+            FP64 once FP32 stalls), and the sweep's members of side <= 256 as
+            one batch to residual 1e-5: p50/p99 seconds per solve
+  serving   a Poisson stream of cavity and channel solves to residual 1e-7
+            through the continuous-batching server; a subset solved four
+            ways (batched or one at a time, FP32 then FP64 or FP64 only)
   cpu_baseline  the FP64 CPU oracle on a bounded sample (rank 0, N = 1)
 `--impl reference` times that oracle alone (the reference arm).
 Multi-GPU: instances are independent, so each rank advances its own copy of
@@ -56,9 +66,13 @@ def parse():
     ap.add_argument("--chunk", type=int, default=None, help="time steps per bench step")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--tile", default=None, help="bx,by[,pair] for every lattice (default: built-in)")
-    ap.add_argument("--serving", type=int, default=16,
-                    help="requests in the bounded serving run (0 to skip)")
+    ap.add_argument("--tile", default=None, help="bx,by[,pair] for every lattice (default: batch autotuner)")
+    ap.add_argument("--no-tune", action="store_true", help="keep the built-in launch shapes")
+    ap.add_argument("--serving", type=int, default=200,
+                    help="requests in the served Poisson stream (0 to skip)")
+    ap.add_argument("--serving-compare", type=int, default=12,
+                    help="requests of the stream also solved batched/one at a time x FP32/FP64")
+    ap.add_argument("--no-steady", action="store_true", help="skip the time-to-steady runs")
     return ap.parse_args()
 
 
@@ -205,42 +219,130 @@ def cpu_baseline(cfgs, budget_s=12.0):
                       f"{el:.1f} s"}
 
 
-def serving_run(n, dev):
-    """Bounded continuous-batching run: a seeded Poisson stream of n cavity
-    and channel solves (sides 48..160, FP32 deviation storage, residual
-    target 1e-5 over 1000-step windows, cap 60,000 steps), served by
-    serve.Server; the same requests are then solved one at a time in FP64
-    with plain per-step launches (the sequential baseline)."""
+def _requests(mix, precision):
     from paper_1809_08683_gb300 import serve
-    mix = W.serving_mix(n=n, seed=1810, min_side=48, max_side=160, mean_interarrival=0.05,
-                        tol=1e-5, max_steps=60000, precision=1)
-    reqs = [serve.Request(rid=m["rid"], cfg=m["cfg"], arrival=m["arrival"], tol=m["tol"],
-                          max_steps=m["max_steps"]) for m in mix]
-    srv = serve.Server(max_slots=64, chunk=1000, graph_steps=100)
-    srv.run(reqs)
-    lat = [r.latency for r in reqs]
-    served = {"requests": n, "wall_s": srv.wall, "mlups": srv.node_steps / srv.wall / 1e6,
-              **{k + "_latency_s": v for k, v in serve.percentiles(lat).items()},
-              "converged": sum(r.status == "converged" for r in reqs),
-              "capped": sum(r.status == "capped" for r in reqs),
-              "unstable": sum(r.status == "unstable" for r in reqs)}
-    seq_reqs = []
-    t0 = time.perf_counter()
-    node_steps = 0
+    out = []
     for m in mix:
         c = dict(m["cfg"])
-        c["precision"] = 0
-        r = serve.Request(rid=m["rid"], cfg=c, tol=m["tol"], max_steps=m["max_steps"])
-        serve.solve_sequential(r)
-        node_steps += r.steps * r.nodes
-        seq_reqs.append(r)
-    seq_wall = time.perf_counter() - t0
-    solve = [r.result.get("solve_s") for r in seq_reqs]
-    served["sequential_fp64"] = {"wall_s": seq_wall, "mlups": node_steps / seq_wall / 1e6,
-                                 **{k + "_solve_s": v for k, v in serve.percentiles(solve).items()}}
-    served["speedup_vs_sequential_fp64"] = seq_wall / srv.wall
-    served["mix"] = "config-5 style Poisson stream (mean 50 ms), cavities and channels, sides 48..160, seed 1810"
-    return served
+        c["precision"] = precision
+        out.append(serve.Request(rid=m["rid"], cfg=c, arrival=m["arrival"], tol=m["tol"], max_steps=m["max_steps"]))
+    return out
+
+
+def _field_errors(a, b):
+    """Errors of fields a against reference fields b: velocity relative to
+    the largest speed, rho - 1 and T - 1 each relative to their own size."""
+    umax = max(np.hypot(b["ux"], b["uy"]).max(), 1e-300)
+    return {"u": float(max(np.abs(a["ux"] - b["ux"]).max(), np.abs(a["uy"] - b["uy"]).max()) / umax),
+            "rho_dev": float(np.abs(a["rho"] - b["rho"]).max() / max(np.abs(b["rho"] - 1.0).max(), 1e-300)),
+            "T_dev": float(np.abs(a["T"] - b["T"]).max() / max(np.abs(b["T"] - 1.0).max(), 1e-300))}
+
+
+SERVING_SIDES = (24, 96)
+
+
+def serving_run(n, n_compare):
+    """Continuous batching of a seeded Poisson stream of n cavity and channel
+    solves (mean inter-arrival 50 ms, sides 24..96, FP32 deviation storage
+    finished in FP64 where FP32 stalls, residual target 1e-7, cap 600,000
+    steps), honouring arrival times.  The first n_compare requests are also
+    solved three more ways for the attribution of the speed-up: batched in
+    FP64 only, and one at a time with per-step launches, FP32-then-FP64 and
+    FP64 only (all with every request available at once); each FP32 result
+    is compared with its own FP64 solve."""
+    from paper_1809_08683_gb300 import serve
+    mix = W.serving_mix(n=n, seed=1810, min_side=SERVING_SIDES[0], max_side=SERVING_SIDES[1],
+                        mean_interarrival=0.05, tol=1e-7, max_steps=600_000, precision=1)
+    reqs = _requests(mix, 1)
+    srv = serve.Server(max_slots=64, chunk=1000, graph_steps=100)
+    srv.run(reqs, realtime=True)
+    lat = [r.latency for r in reqs]
+    node_steps = sum(r.steps * r.nodes for r in reqs)
+    out = {"requests": n, "tol": 1e-7, "wall_s": srv.wall, "mlups": node_steps / srv.wall / 1e6,
+           **{k + "_latency_s": v for k, v in serve.percentiles(lat).items()},
+           "converged": sum(r.status == "converged" for r in reqs),
+           "capped": sum(r.status == "capped" for r in reqs),
+           "unstable": sum(r.status == "unstable" for r in reqs),
+           "finished_in_fp64": sum(r.switched_at is not None for r in reqs),
+           "host_overhead": srv.host_overhead, "host_s": srv.host_s, "chunks": srv.chunks,
+           "batch_rebuilds": srv.rebuilds,
+           "mix": f"Poisson stream (mean 50 ms), cavities and channels, sides {SERVING_SIDES[0]}.."
+                  f"{SERVING_SIDES[1]}, seed 1810, FP32 then FP64 where FP32 stalls"}
+    if n_compare <= 0:
+        return out
+    sub = mix[:n_compare]
+    cells = {}
+    # batched, FP32 then FP64 (the same requests as above, all at once)
+    b32 = _requests(sub, 1)
+    s32 = serve.Server(max_slots=64, chunk=1000, graph_steps=100, keep_fields=True)
+    s32.run(b32, realtime=False)
+    cells["batched_fp32_then_fp64"] = s32.wall
+    b64 = _requests(sub, 0)
+    s64 = serve.Server(max_slots=64, chunk=1000, graph_steps=100, keep_fields=True)
+    s64.run(b64, realtime=False)
+    cells["batched_fp64"] = s64.wall
+    for prec, name in ((1, "sequential_fp32_then_fp64"), (0, "sequential_fp64")):
+        t0 = time.perf_counter()
+        for r in _requests(sub, prec):
+            serve.solve_sequential(r)
+        cells[name] = time.perf_counter() - t0
+    errs = []
+    for a, b in zip(b32, b64):
+        if a.status == "converged" and b.status == "converged":
+            e = _field_errors(a.result["fields"], b.result["fields"])
+            if "nusselt" in b.result:
+                e["nu"] = abs(a.result["nusselt"] / b.result["nusselt"] - 1.0)
+            errs.append(e)
+    worst = {k: max((e[k] for e in errs if k in e), default=None) for k in ("u", "rho_dev", "T_dev", "nu")}
+    out["compare"] = {
+        "requests": n_compare, "wall_s": cells,
+        "speedup_vs_sequential_fp64": cells["sequential_fp64"] / cells["batched_fp32_then_fp64"],
+        "from_batching_fp32": cells["sequential_fp32_then_fp64"] / cells["batched_fp32_then_fp64"],
+        "from_fp32_batched": cells["batched_fp64"] / cells["batched_fp32_then_fp64"],
+        "converged": {"fp32_then_fp64": sum(r.status == "converged" for r in b32),
+                      "fp64": sum(r.status == "converged" for r in b64)},
+        "max_error_vs_own_fp64_solve": worst, "compared": len(errs),
+        "within_tolerance": all((e["u"] <= 1e-4 and e["rho_dev"] <= 1e-3 and e["T_dev"] <= 1e-3
+                                 and e.get("nu", 0.0) <= 5e-3) for e in errs)}
+    return out
+
+
+def steady_cavity512(tol=1e-8):
+    """Config 3: the 512^2 heated cavity at Ra = 1e6, eps = 0.6, ideal gas,
+    Sutherland viscosity, run from rest to residual `tol` in FP32 deviation
+    storage, finished in FP64 once FP32 stalls; its lone launch shape from
+    the autotuner.  Nu_ave and p*_ave against Table 2."""
+    from paper_1809_08683_gb300 import autotune, serve
+    cfg = W.cavity(N=512, Ra=1e6, eps=0.6, precision=1)
+    req = serve.Request(rid=0, cfg=cfg, tol=tol, max_steps=3_000_000)
+    srv = serve.Server(max_slots=1, chunk=1000, graph_steps=1000, tile_fn=lambda c: autotune.tune(c, steps=10))
+    for prec in (1, 0):                 # tune outside the timed solve
+        autotune.tune(dict(cfg, precision=prec), steps=10)
+    srv.run([req], realtime=False)
+    nu, ps = req.result.get("nusselt"), req.result.get("pstar")
+    return {"workload": "cavity_512x512_Ra1e6_eps0.6", "tol": tol, "status": req.status, "s": req.latency,
+            "steps": req.steps, "fp64_from_step": req.switched_at, "nu": nu, "pstar": ps,
+            "table2": {"nu": 8.7406, "pstar": 0.91820},
+            "nu_vs_table2": None if nu is None else nu / 8.7406 - 1.0,
+            "pstar_vs_table2": None if ps is None else ps / 0.91820 - 1.0}
+
+
+def steady_sweep_subset(tol=1e-5, max_side=256):
+    """Config 4's members of side <= max_side served as one batch from rest
+    to residual `tol` (FP32, FP64 finish where FP32 stalls): p50/p99 of the
+    per-member time to steady."""
+    from paper_1809_08683_gb300 import serve
+    cfgs = [c for c in W.batched_sweep(precision=1) if c["nx"] <= max_side]
+    reqs = [serve.Request(rid=i, cfg=c, tol=tol, max_steps=1_000_000) for i, c in enumerate(cfgs)]
+    srv = serve.Server(max_slots=len(reqs), chunk=1000, graph_steps=1000)
+    srv.run(reqs, realtime=False)
+    return {"workload": f"batched_sweep_96_cavities members of side <= {max_side}", "members": len(reqs),
+            "tol": tol, **{k + "_s": v for k, v in serve.percentiles([r.latency for r in reqs]).items()},
+            "wall_s": srv.wall, "converged": sum(r.status == "converged" for r in reqs),
+            "capped": sum(r.status == "capped" for r in reqs),
+            "unstable": sum(r.status == "unstable" for r in reqs),
+            "finished_in_fp64": sum(r.switched_at is not None for r in reqs),
+            "mlups": sum(r.steps * r.nodes for r in reqs) / srv.wall / 1e6}
 
 
 def max_over_ranks(value, world, dist=None, device=None):
@@ -296,7 +398,7 @@ def main():
         return run_reference(args)
     import torch
     import torch.distributed as dist
-    from paper_1809_08683_gb300 import lbm
+    from paper_1809_08683_gb300 import autotune, lbm
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -311,14 +413,22 @@ def main():
     cfgs, desc, chunk = workload(args.workload, args.precision)
     chunk = args.chunk or chunk
     stream = torch.cuda.Stream(device=dev)
-    lats = [lbm.Lattice(c, stream=stream, device=dev) for c in cfgs]
+    with torch.cuda.stream(stream):
+        lats = [lbm.Lattice(c, stream=stream, device=dev) for c in cfgs]
+    tuned = None
     if args.tile:
         t = [int(v) for v in args.tile.split(",")]
         for lat in lats:
             lat.set_tile(t[0], t[1], t[2] if len(t) > 2 else 0)
-    batch = lbm.Batch(lats, graph_steps=0)
+    elif not args.no_tune:
+        best, res = autotune.tune_batch(lats)
+        tuned = {"pick": None if best is None else list(best), "ms_per_step": {
+            ("default" if k is None else ",".join(map(str, k))): v for k, v in res.items()},
+            "default_ms": res[None], "pick_ms": res[best]}
     nodes = sum(c["nx"] * c["ny"] for c in cfgs)
     prec = int(cfgs[0].get("precision", 0))
+    graph_steps = chunk if chunk % 2 == 0 else 0
+    batch = lbm.Batch(lats, graph_steps=graph_steps)
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -326,19 +436,16 @@ def main():
             dist.barrier()
 
     for _ in range(args.warmup):
-        batch.step_profiled(chunk)
+        batch.step(chunk)
     barrier()
 
-    t_collide = t_wall = 0.0
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
         barrier()
         ev0.record(stream)
         for _ in range(args.steps):
-            a, b = batch.step_profiled(chunk)
-            t_collide += a
-            t_wall += b
+            batch.step(chunk)
         ev1.record(stream)
         ev1.synchronize()
         barrier()
@@ -350,15 +457,29 @@ def main():
     value = whole_job_mlups(nodes, steps_total, world, ms)
     clocks = clk.summary()
 
+    # the same batch with per-step launches and events: fused / wall-pass split
+    pbatch = lbm.Batch(lats, graph_steps=0)
+    psteps = min(steps_total, 5 * chunk)
+    pbatch.step_profiled(chunk)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    t_collide, t_wall = pbatch.step_profiled(psteps)
+    e1.record(stream)
+    e1.synchronize()
+    pbatch.close()
+    ungraphed = {"value": nodes * psteps / (e0.elapsed_time(e1) * 1e-3) / 1e6, "steps": psteps,
+                 "fused_ms_per_step": t_collide / psteps, "wall_pass_ms_per_step": t_wall / psteps}
+
     # fused kernel against the HBM roofline
     peak, peak_kind = read_peaks()
-    avg_collide_ms = t_collide / steps_total
+    avg_collide_ms = t_collide / psteps
     alg_bytes = nodes * BYTES_PER_NODE[prec]
     achieved = alg_bytes / (avg_collide_ms * 1e-3) / 1e9
     kernels = sorted({KERNEL_OF_PAIR[lat.tile()[2]] for lat in lats})
     kernel = "+".join(kernels)
-    n_collide_launches = len({lat.tile()[:3:2] for lat in lats})  # one launch per (width, kind) group
-    gpu_launches = args.steps * chunk * (n_collide_launches + 1)
+    n_collide_launches = len({(lat.tile()[0], lat.tile()[2], lat.cfg.get("precision", 0)) for lat in lats})
+    gpu_launches = steps_total * (n_collide_launches + 1)
     traffic = read_traffic(desc["workload"], kernel)
 
     # end to end through the public API with host buffers
@@ -374,6 +495,7 @@ def main():
             host_in.append(fields)
         host_out = [[torch.empty((c["ny"], c["nx"]), dtype=torch.float64).pin_memory().numpy()
                      for _ in range(5)] for c in cfgs]
+
         def e2e_step():
             for lat, f in zip(lats, host_in):
                 lat.init_macros(*f)
@@ -396,18 +518,22 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(cfgs)
 
+    batch.close()
+    for lat in lats:
+        lat.close()
+    lats, batch = [], None
+    torch.cuda.empty_cache()
+
+    steady = None
+    if rank == 0 and not args.no_steady and args.workload == "batched_sweep":
+        steady = {"cavity512": steady_cavity512(), "sweep_subset": steady_sweep_subset()}
     serving = None
     if rank == 0 and args.serving > 0:
-        batch.close()
-        for lat in lats:
-            lat.close()
-        lats, batch = [], None
-        torch.cuda.empty_cache()
-        serving = serving_run(args.serving, dev)
+        serving = serving_run(args.serving, args.serving_compare)
 
     if rank == 0:
         desc = dict(desc)
-        desc.update({"nodes": nodes, "time_steps_per_bench_step": chunk,
+        desc.update({"nodes": nodes, "time_steps_per_bench_step": chunk, "graph_steps": graph_steps,
                      "l2": "state larger than L2 (no flush)" if alg_bytes > 2 * 129e6 else "state may be L2-resident"})
         out = {
             "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
@@ -417,15 +543,12 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
                          "kernel": kernel, "alg_bytes_per_launch": alg_bytes,
-                         "avg_launch_ms": avg_collide_ms, "wall_pass_ms_per_step": t_wall / steps_total},
+                         "avg_launch_ms": avg_collide_ms, "wall_pass_ms_per_step": t_wall / psteps},
+            "autotune": tuned, "ungraphed": ungraphed,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clocks,
-            "serving": serving,
+            "time_to_steady": steady, "serving": serving,
         }
         print(json.dumps(out))
-    if batch is not None:
-        batch.close()
-    for lat in lats:
-        lat.close()
     if world > 1:
         dist.destroy_process_group()
     return 0

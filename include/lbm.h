@@ -194,7 +194,8 @@ lbm_status lbm_wait_selftest(lbm_ctx* ctx, long long limit_cycles);
  * strips of 60 columns, two neighbouring nodes per lane in packed FP32,
  * bx = 60, 120 or 240.  pair = 0 and pair = 4 shapes of any width give
  * identical results; pairs 1-3 and 5 agree with them to FP32 rounding (their
- * arithmetic is contracted differently).
+ * arithmetic is contracted differently).  (bx, by, pair) = (0, 0, 0)
+ * restores the default shape, which batches may then shorten.
  * Used by the autotuner. */
 lbm_status lbm_set_tile(lbm_ctx* ctx, int bx, int by, int pair);
 

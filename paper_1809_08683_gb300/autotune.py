@@ -113,3 +113,44 @@ def apply(lattices, steps: int = 20):
     for lat in lattices:
         bx, by, pr = tune(lat.cfg, steps=steps, stream=lat.stream)
         lat.set_tile(bx, by, pr)
+
+
+# Shapes tried for a whole batch: paired block strips with run lengths
+# around the built-in batch length, block strips, and the built-in default
+# (None: each member's default shape, runs shortened by the batch builder).
+BATCH_SHAPES = (None, (128, 16, 1), (128, 24, 1), (128, 32, 1), (128, 48, 1), (256, 32, 1), (128, 24, 0))
+
+
+def measure_batch(lattices, shape, steps: int = 10, warmup: int = 3) -> float:
+    """Milliseconds per time step of the whole batch (fused and wall-pass
+    launches, CUDA events) with `shape` applied to every member, or each
+    member's default shape for None.  The shape stays applied."""
+    for lat in lattices:
+        if shape is None:
+            lat.set_tile(0, 0, 0)
+        else:
+            lat.set_tile(*shape)
+    batch = lbm.Batch(lattices, graph_steps=0)
+    batch.step_profiled(warmup)
+    a, b = batch.step_profiled(steps)
+    batch.close()
+    return (a + b) / steps
+
+
+def tune_batch(lattices, shapes=BATCH_SHAPES, steps: int = 10):
+    """Time the batch under every candidate shape that all members accept
+    and leave the fastest applied.  Returns (best, {shape: ms per step});
+    None stands for the built-in default."""
+    results = {}
+    for shape in shapes:
+        if shape is not None:
+            if shape[2] in (1, 2, 3, 5) and any(int(l.cfg.get("precision", 0)) != 1 for l in lattices):
+                continue
+        results[shape] = measure_batch(lattices, shape, steps)
+    best = min(results, key=results.get)
+    for lat in lattices:
+        if best is None:
+            lat.set_tile(0, 0, 0)
+        else:
+            lat.set_tile(*best)
+    return best, results

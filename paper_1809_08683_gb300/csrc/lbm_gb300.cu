@@ -2170,6 +2170,34 @@ std::vector<Work> make_work(const lbm_config& c, int inst, int bx, int by, int p
     return v;
 }
 
+// Shorter runs at the end of a launch: the CTAs of one launch start as
+// resident slots free up, so the launch ends when the last ones finish, and
+// with runs of equal length the GPU idles for up to one run at the end.
+// The last `resident` work items (one fill of the GPU) are cut into up to
+// four runs of at least 6 rows each (shorter runs re-stage too many halo
+// rows), placed last; that shortens the idle end to about a quarter of a
+// run.  Measured on the 96-cavity batch (runs of 32 rows): fused launch
+// 1.138 -> 1.123 ms; 16 cavities of 1024^2: 0.503 -> 0.488 ms.  Which CTA
+// updates a node does not change its arithmetic, so the results are the
+// same bits.
+void split_tail(std::vector<Work>& v, long long resident) {
+    if (resident <= 0 || (long long)v.size() <= resident) return;
+    const size_t first = v.size() - (size_t)resident;
+    std::vector<Work> tail(v.begin() + first, v.end());
+    v.resize(first);
+    for (int part = 0; part < 4; ++part)
+        for (const Work& w : tail) {
+            const int rows = w.y1 - w.y0;
+            const int parts = std::max(1, std::min(4, rows / 6));
+            if (part >= parts) continue;
+            Work u = w;
+            u.y0 = w.y0 + rows * part / parts;
+            u.y1 = w.y0 + rows * (part + 1) / parts;
+            u.dir = (w.dir + part) & 1;
+            v.push_back(u);
+        }
+}
+
 std::vector<BWork> make_bwork(const lbm_config& c, int inst, int par) {
     std::vector<BWork> v;
     const int px = c.wall[LBM_WALL_W].periodic != 0, py = c.wall[LBM_WALL_S].periodic != 0;
@@ -2285,9 +2313,14 @@ lbm_status encode_windows(lbm_ctx* c) {
     return LBM_OK;
 }
 
+long long resident_ctas(int vi, bool fp32);
+int variant_index(int bx, int pair);
+bool is_fp32(const lbm_ctx* c);
+
 lbm_status upload_work(lbm_ctx* c) {
     if (c->d_work) { cudaFree(c->d_work); c->d_work = nullptr; }
     c->h_work = make_work(c->cfg, 0, c->bx, c->by, 0, 0);
+    split_tail(c->h_work, resident_ctas(variant_index(c->bx, c->pair), is_fp32(c)));
     c->n_work = (int)c->h_work.size();
     CUDA_TRY(cudaMalloc(&c->d_work, c->h_work.size() * sizeof(Work)));
     CUDA_TRY(cudaMemcpyAsync(c->d_work, c->h_work.data(), c->h_work.size() * sizeof(Work),
@@ -2894,6 +2927,16 @@ lbm_status lbm_copy_state(lbm_ctx* d, const lbm_ctx* s) {
 
 lbm_status lbm_set_tile(lbm_ctx* c, int bx, int by, int pair) {
     if (!c) return fail(LBM_EINVAL, "null ctx");
+    if (bx == 0 && by == 0 && pair == 0) {
+        // back to the default shape of lbm_create / lbm_set_eos
+        default_shape(c->cfg, c->mc, c->bx, c->pair);
+        c->by = default_rows(c->cfg, c->pair);
+        c->tile_set = false;
+        lbm_status st = upload_work(c);
+        if (st != LBM_OK) return st;
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        return LBM_OK;
+    }
     if (pair != 0 && pair != 4 && c->cfg.precision != LBM_FP32_DEV)
         return fail(LBM_EINVAL, "pair 1-3 and 5 need FP32 storage");
     if (variant_index(bx, pair) < 0)
@@ -3233,8 +3276,11 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, int graph_steps, lbm_ba
     for (int pr = 0; pr < 2; ++pr)
         for (int bi = 0; bi < kVariants; ++bi)
             for (int mc = 0; mc < kModels; ++mc)
+            {
                 std::stable_sort(groups[pr][bi][mc].begin(), groups[pr][bi][mc].end(),
                                  [](const Work& a, const Work& b) { return a.y1 - a.y0 > b.y1 - b.y0; });
+                if (!groups[pr][bi][mc].empty()) split_tail(groups[pr][bi][mc], resident_ctas(bi, pr == 1));
+            }
     for (int pr = 0; pr < 2; ++pr)
         for (int bi = 0; bi < kVariants; ++bi)
             for (int mc = 0; mc < kModels; ++mc) {

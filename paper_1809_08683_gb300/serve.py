@@ -13,10 +13,12 @@ so a small request is not held back behind a large one that does not fit
 yet.  The batch is rebuilt only when the resident set changes.
 
 Precision: a request whose configuration asks for FP32 deviation storage is
-stepped in FP32 until its residual falls below ``fp32_floor`` (stochastic
-rounding keeps FP32 residuals from falling much below 1e-6); if its target
-is tighter, the solve is finished in FP64 from the FP32 state
-(lbm_copy_state), so that every result meets its stated target.  A
+stepped in FP32 while FP32 makes progress; stochastic rounding leaves FP32
+residuals on a noise floor (about 1e-6 for heated cavities, 1e-5 for
+channels, whose temperature variation is small).  If the target lies below
+what FP32 reaches (the residual stops falling below ``fp32_stall``), the
+solve is finished in FP64 from the FP32 state (lbm_copy_state), so that
+every result meets its stated target.  A
 request's result is bitwise the same alone and in any mix: per-node
 arithmetic does not depend on the batch, residual checks fall on the same
 step counts, and stochastic rounding draws from (node, absolute step) only.
@@ -45,6 +47,7 @@ class Request:
     status: str = "pending"
     switched_at: int | None = None   # step count at which an FP32 solve moved to FP64
     result: dict = field(default_factory=dict)
+    history: list = field(default_factory=list)   # residual after each chunk
 
     @property
     def latency(self):
@@ -65,6 +68,18 @@ def summarise(lat, req):
     if len(dirichlet) >= 2 and len(Ts) >= 2:
         out["nusselt"] = lat.nusselt(max(dirichlet, key=lambda s: walls[s]["T"]))
     return out
+
+
+def fp32_stalled(history, ceiling=1e-4, window=20, gain=0.8):
+    """Whether an FP32 solve has reached what FP32 storage can resolve: its
+    residual is below `ceiling` and the best residual of the last `window`
+    checks is no better than `gain` times the best of the `window` before.
+    Stochastic rounding puts the FP32 noise floor near 1e-6 for heated
+    cavities and 1e-5 for channels; above `ceiling` a slow or oscillating
+    start-up transient is not taken for that floor.  None: never."""
+    if ceiling is None or len(history) < 2 * window or history[-1] >= ceiling:
+        return False
+    return min(history[-window:]) > gain * min(history[-2 * window:-window])
 
 
 def _fp64(cfg):
@@ -116,14 +131,14 @@ class Server:
     device memory free at construction that resident lattices may take; the
     memory free at each admission (minus the rest of the device as
     headroom) is checked as well, so memory that other work takes or frees
-    later is seen.  fp32_floor: the residual below which FP32 storage is not
-    trusted to converge; None keeps FP32 to the end (targets must then be
-    above the floor).  starvation_s: a request that has waited this long
-    stops later arrivals from overtaking it (None: never)."""
+    later is seen.  fp32_stall: the residual below which an FP32 solve that
+    stops improving moves to FP64 (fp32_stalled); None keeps FP32 to the
+    end.  starvation_s: a request that has waited this long stops later
+    arrivals from overtaking it (None: never)."""
 
     def __init__(self, max_slots: int = 64, mem_fraction: float = 0.85, chunk: int = 1000,
                  graph_steps: int = 100, stream=None, tile_fn=None, keep_fields: bool = False,
-                 fp32_floor: float | None = 3e-6, starvation_s: float | None = None):
+                 fp32_stall: float | None = 1e-4, starvation_s: float | None = None):
         import torch
         self.torch = torch
         self.max_slots = max_slots
@@ -133,7 +148,7 @@ class Server:
         self.stream = stream if stream is not None else torch.cuda.Stream()
         self.tile_fn = tile_fn
         self.keep_fields = keep_fields
-        self.fp32_floor = fp32_floor
+        self.fp32_stall = fp32_stall
         self.starvation_s = starvation_s
         free, total = torch.cuda.mem_get_info()
         self.total = total
@@ -144,6 +159,9 @@ class Server:
         self.gpu_ms = 0.0          # device time of the stepping, summed over chunks
         self.chunks = 0
         self.rebuilds = 0
+        # host seconds between one chunk's diagnostics and the next chunk's
+        # launch (the device idles), and where they went
+        self.host_s = {"between_chunks": 0.0, "admit": 0.0, "retire": 0.0, "rebuild": 0.0}
         self.log = []
 
     # -- device memory ----------------------------------------------------
@@ -184,8 +202,10 @@ class Server:
         dirty = True
         timer = _Timer(self.stream)
         t0 = time.perf_counter()
+        t_diag = None           # when the last chunk's diagnostics returned
         while pending or resident:
             now = time.perf_counter() - t0
+            ta = time.perf_counter()
             # admission: first fit in arrival order
             i = 0
             while i < len(pending) and len(resident) < self.max_slots:
@@ -206,6 +226,7 @@ class Server:
                 r.status = "running"
                 resident.append(_Slot(r, lat, nbytes))
                 dirty = True
+            self.host_s["admit"] += time.perf_counter() - ta
             if not resident:
                 future = [r for r in pending if realtime and r.arrival > now]
                 if not future:
@@ -214,15 +235,20 @@ class Server:
                 time.sleep(max(0.0, min(0.01, future[0].arrival - now)))
                 continue
             if dirty:
+                tb = time.perf_counter()
                 if batch is not None:
                     batch.close()
                 batch = lbm.Batch([s.lat for s in resident], graph_steps=self.graph_steps)
                 self.rebuilds += 1
                 dirty = False
+                self.host_s["rebuild"] += time.perf_counter() - tb
+            if t_diag is not None:
+                self.host_s["between_chunks"] += time.perf_counter() - t_diag
             timer.start()
             batch.step(self.chunk)
             timer.stop()
             diags = batch.diagnostics(snapshot=True)
+            t_diag = time.perf_counter()
             self.gpu_ms += timer.ms()
             self.chunks += 1
             self.node_steps += self.chunk * sum(s.req.nodes for s in resident)
@@ -234,24 +260,23 @@ class Server:
                     r.status = "unstable"
                     r.result["error"] = f"lbm status {st}"
                 else:
-                    r.result["residual"] = d["residual"]
+                    res = d["residual"]
+                    r.result["residual"] = res
+                    r.history.append(res)
                     fp32 = int(slot.lat.cfg.get("precision", 0)) == lbm.FP32_DEV
-                    target = r.tol
-                    if fp32 and self.fp32_floor is not None:
-                        target = max(r.tol, self.fp32_floor)
-                    if r.steps >= r.min_steps and d["residual"] < target:
-                        if target > r.tol and self._switch_to_fp64(slot):
-                            r.switched_at = r.steps
-                            dirty = True
-                        else:
-                            r.converged = True
-                            r.status = "converged"
+                    if r.steps >= r.min_steps and res < r.tol:
+                        r.converged = True
+                        r.status = "converged"
+                    elif fp32 and fp32_stalled(r.history, self.fp32_stall) and self._switch_to_fp64(slot):
+                        r.switched_at = r.steps
+                        dirty = True
                     if r.status == "running" and r.steps >= r.max_steps:
                         r.status = "capped"
                 if r.status == "running":
                     keep.append(slot)
                     continue
                 r.finished = time.perf_counter() - t0
+                tr = time.perf_counter()
                 if r.status != "unstable":
                     r.result.update(summarise(slot.lat, r))
                     if self.keep_fields:
@@ -259,6 +284,7 @@ class Server:
                 self.in_use -= slot.bytes
                 slot.lat.close()
                 dirty = True
+                self.host_s["retire"] += time.perf_counter() - tr
             if dirty and batch is not None:
                 batch.close()
                 batch = None
@@ -291,34 +317,33 @@ class Server:
         return max(0.0, 1.0 - self.gpu_ms * 1e-3 / self.wall) if getattr(self, "wall", 0) else None
 
 
-def solve_sequential(req: Request, chunk: int = 1000, keep_fields: bool = False, fp32_floor: float | None = 3e-6):
+def solve_sequential(req: Request, chunk: int = 1000, keep_fields: bool = False, fp32_stall: float | None = 1e-4):
     """Plain per-request solve: the lattice alone, per-step launches, the
-    same residual schedule (and the same FP32-to-FP64 finish for targets
-    below fp32_floor).  The baseline the batched server is compared to."""
+    same residual schedule (and the same move from FP32 to FP64 once FP32
+    stalls).  The baseline the batched server is compared to."""
+    t0 = time.perf_counter()
     lat = lbm.Lattice(req.cfg)
     lat.diagnostics(snapshot=True)
-    t0 = time.perf_counter()
     while True:
         lat.step(chunk)
         req.steps += chunk
         d = lat.diagnostics(snapshot=True)
-        req.result["residual"] = d["residual"]
-        fp32 = int(lat.cfg.get("precision", 0)) == lbm.FP32_DEV
-        target = max(req.tol, fp32_floor) if (fp32 and fp32_floor is not None) else req.tol
-        if req.steps >= req.min_steps and d["residual"] < target:
-            if target > req.tol:
-                lat64 = lbm.Lattice(_fp64(lat.cfg))
-                lat64.copy_state_from(lat)
-                lat.close()
-                lat = lat64
-                req.switched_at = req.steps
-                continue
+        res = d["residual"]
+        req.result["residual"] = res
+        req.history.append(res)
+        if req.steps >= req.min_steps and res < req.tol:
             req.converged = True
             req.status = "converged"
             break
         if req.steps >= req.max_steps:
             req.status = "capped"
             break
+        if int(lat.cfg.get("precision", 0)) == lbm.FP32_DEV and fp32_stalled(req.history, fp32_stall):
+            lat64 = lbm.Lattice(_fp64(lat.cfg))
+            lat64.copy_state_from(lat)
+            lat.close()
+            lat = lat64
+            req.switched_at = req.steps
     req.result.update(summarise(lat, req))
     if keep_fields:
         req.result["fields"] = lat.macros()

@@ -70,3 +70,33 @@ def test_apply_sets_every_lattice(tmp_path, monkeypatch):
     autotune.apply(lats, steps=2)
     for lat in lats:
         assert lat.tile == max(autotune.candidates(lat.cfg), key=lambda t: t[0] + t[1])
+
+
+def test_tune_batch_picks_fastest_shape_and_applies_it(monkeypatch):
+    timings = {None: 1.30, (128, 16, 1): 1.31, (128, 24, 1): 1.28, (128, 32, 1): 1.25, (128, 48, 1): 1.27,
+               (256, 32, 1): 1.40, (128, 24, 0): 1.39}
+    seen = []
+
+    def fake_measure(lattices, shape, steps=10, warmup=3):
+        seen.append(shape)
+        return timings[shape]
+
+    class FakeLattice:
+        def __init__(self, precision):
+            self.cfg, self.tiles = {"precision": precision}, []
+
+        def set_tile(self, *t):
+            self.tiles.append(t)
+
+    monkeypatch.setattr(autotune, "measure_batch", fake_measure)
+    lats = [FakeLattice(1), FakeLattice(1)]
+    best, res = autotune.tune_batch(lats)
+    assert best == (128, 32, 1) and res[best] == 1.25
+    assert seen == list(autotune.BATCH_SHAPES)
+    assert all(l.tiles[-1] == (128, 32, 1) for l in lats)
+    # an FP64 member rules out the packed-FP32 shapes; the default can win
+    seen.clear()
+    lats = [FakeLattice(1), FakeLattice(0)]
+    best, res = autotune.tune_batch(lats)
+    assert set(res) == {None, (128, 24, 0)} and best is None
+    assert all(l.tiles[-1] == (0, 0, 0) for l in lats)

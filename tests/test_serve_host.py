@@ -237,15 +237,16 @@ def test_admission_sees_memory_taken_by_others(server_factory):
 
 def test_fp32_solve_below_its_floor_finishes_in_fp64(server_factory):
     make, trace = server_factory
-    # FP32 stalls at a residual of 1e-6; the target is 1e-8: the solve
-    # switches to FP64 storage once below the floor (3e-6) and finishes there
-    reqs = make_requests([(0.0, 100, 0.1, None, 20000), (0.0, 100, 0.1, None, 20000)],
+    # FP32 stalls at a residual of 1e-6 (reached after 6000 steps); the
+    # target is 1e-8: once 20 checks bring no gain over the 20 before, the
+    # solve moves to FP64 storage and finishes there
+    reqs = make_requests([(0.0, 100, 0.1, None, 80000), (0.0, 100, 0.1, None, 80000)],
                          precision=1, tol=1e-8, floor=1e-6)
     reqs[1].tol = 2e-5                       # above the floor: stays FP32
-    srv = make(10_000, max_slots=8, mem_fraction=1.0, chunk=1000, graph_steps=0, fp32_floor=3e-6)
+    srv = make(10_000, max_slots=8, mem_fraction=1.0, chunk=1000, graph_steps=0, fp32_stall=1e-4)
     srv.run(reqs, realtime=False)
     assert [r.status for r in reqs] == ["converged", "converged"]
-    assert reqs[0].switched_at == 6000 and reqs[0].steps == 9000
+    assert reqs[0].switched_at == 40000 and reqs[0].steps == 41000
     assert reqs[1].switched_at is None and reqs[1].steps == 5000
     assert (0, 0) in trace["created"] and (1, 0) not in trace["created"]
     assert trace["copied"] == [0]
@@ -254,7 +255,33 @@ def test_fp32_solve_below_its_floor_finishes_in_fp64(server_factory):
 
 def test_fp32_without_a_floor_caps(server_factory):
     make, _ = server_factory
-    reqs = make_requests([(0.0, 100, 0.1, None, 20000)], precision=1, tol=1e-8, floor=1e-6)
-    srv = make(10_000, max_slots=8, mem_fraction=1.0, chunk=1000, graph_steps=0, fp32_floor=None)
+    reqs = make_requests([(0.0, 100, 0.1, None, 60000)], precision=1, tol=1e-8, floor=1e-6)
+    srv = make(10_000, max_slots=8, mem_fraction=1.0, chunk=1000, graph_steps=0, fp32_stall=None)
     srv.run(reqs, realtime=False)
     assert reqs[0].status == "capped" and reqs[0].switched_at is None
+
+
+def test_fp32_plateau_above_the_floor_also_finishes_in_fp64(server_factory):
+    make, trace = server_factory
+    # a channel-like FP32 solve whose noise floor lies at 2e-5: the residual
+    # stops falling and the solve moves to FP64
+    reqs = make_requests([(0.0, 100, 0.5, None, 200000)], precision=1, tol=1e-7, floor=2e-5)
+    srv = make(10_000, max_slots=8, mem_fraction=1.0, chunk=1000, graph_steps=0, fp32_stall=1e-4)
+    srv.run(reqs, realtime=False)
+    r = reqs[0]
+    assert r.status == "converged" and r.switched_at is not None
+    # 0.5 per 1000 steps reaches the 2e-5 floor after 16 chunks; the stall is
+    # seen 40 checks in at the earliest
+    assert 40000 <= r.switched_at <= 60000
+    assert r.steps < r.switched_at + 30000
+
+
+def test_stall_rule():
+    assert not serve.fp32_stalled([1e-5] * 39)                 # too short to tell
+    assert serve.fp32_stalled([1e-5] * 40)                     # flat below the ceiling
+    assert not serve.fp32_stalled([3e-4] * 40)                 # flat above it: a start-up transient
+    decaying = [10 ** (-3 - k / 20) for k in range(40)]        # a decade per 20 checks
+    assert not serve.fp32_stalled(decaying)
+    slow = [10 ** (-3 - k / 100) for k in range(40)]           # a decade per 100 checks: 0.63 per 20
+    assert not serve.fp32_stalled(slow)
+    assert not serve.fp32_stalled([1e-5] * 40, None)
