@@ -224,10 +224,23 @@ const char* lbm_last_error(void);
  * kernel instance, all others the generic one) and one wall-pass launch per
  * precision per step.  A lattice gives the same bits alone or batched.
  * graph_steps > 0 captures that many steps in a CUDA graph that
- * lbm_batch_step replays (nsteps must then be a multiple of graph_steps).
+ * lbm_batch_step replays (nsteps must then be a multiple of graph_steps);
+ * a batch of 4,194,304 nodes or more is captured as two branches, each
+ * stepping about half of the nodes, so that the wall pass of one half
+ * overlaps the fused launches of the other.
  * A member whose EOS class lbm_set_eos changes afterwards makes the batch
  * step fail with LBM_EINVAL: build the batch again. */
 lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, int graph_steps, lbm_batch** out);
+
+/* Add a context as the last member, or remove one (the others keep their
+ * order; a removed context keeps its state and can be stepped alone or
+ * batched again).  The launch tables and the graph are rebuilt, as
+ * lbm_batch_create builds them; the batch handle stays valid and, if the
+ * rebuild fails, unchanged.  Synchronises the batch stream.  LBM_EINVAL for
+ * a context already in (add) or not in (remove) the batch, for one on
+ * another stream, and for removing the last member. */
+lbm_status lbm_batch_add(lbm_batch* b, lbm_ctx* ctx);
+lbm_status lbm_batch_remove(lbm_batch* b, lbm_ctx* ctx);
 lbm_status lbm_batch_step(lbm_batch* b, long nsteps);
 lbm_status lbm_batch_destroy(lbm_batch* b);     /* NULL-safe */
 

@@ -2129,6 +2129,16 @@ constexpr int kModels = 2;  // model classes: lbm::MODEL_ANY, lbm::MODEL_CAVITY
 // mix) then stay one launch per shape.
 constexpr long long kModelMinNodes = 32768;
 
+// The launches of one time step over a set of members: launch groups
+// [precision][variant][model class] as ranges of the batch's work table,
+// wall-pass ranges [precision] of its wall table, and the step counter
+// that the set's last wall-pass launch advances and its fused launches read.
+struct LaunchSet {
+    int w_off[2][kVariants][kModels] = {}, w_cnt[2][kVariants][kModels] = {};
+    int b_off[2] = {0, 0}, b_cnt[2] = {0, 0};
+    long long* counter = nullptr;
+};
+
 struct lbm_batch {
     std::vector<lbm_ctx*> ctxs;
     std::vector<int> models;  // each member's model class when the launch groups were built
@@ -2136,13 +2146,16 @@ struct lbm_batch {
     InstDesc** d_descs = nullptr;
     Work* d_work = nullptr;
     BWork* d_bwork = nullptr;
-    // launch groups: [precision][variant][model class] ranges of d_work; [precision] ranges of d_bwork
-    int w_off[2][kVariants][kModels] = {}, w_cnt[2][kVariants][kModels] = {};
-    int b_off[2] = {0, 0}, b_cnt[2] = {0, 0};
+    // set 0: every member, for per-step launches; sets 1 and 2: the two
+    // halves of the members, replayed on two branches of the graph
+    LaunchSet sets[3];
+    bool split = false;
     long steps = 0;
     int graph_steps = 0;
     cudaGraphExec_t graph = nullptr;
-    long long* d_counter = nullptr;  // batch step counter, advanced on the device
+    cudaStream_t side = nullptr;     // second capture branch
+    cudaEvent_t fork = nullptr, join = nullptr;
+    long long* d_counter = nullptr;  // three step counters, one per launch set, advanced on the device
     DiagJob* d_jobs = nullptr;       // lbm_batch_diagnostics: one job per member, FP32 members first
     double* d_diag_out = nullptr;    // [member][kDiagSlots + 1] sums and status word
     std::vector<int> diag_order;     // members in job order
@@ -3195,48 +3208,86 @@ lbm_status lbm_conserved_sums_static(const lbm_ctx* c, double* out4) {
 // batched stepping
 // ------------------------------------------------------------------------
 
-static void batch_launch_collide(lbm_batch* b, int par) {
+static void batch_launch_collide(lbm_batch* b, const LaunchSet& ls, int par, cudaStream_t st) {
     for (int pr = 0; pr < 2; ++pr)
         for (int vi = 0; vi < kVariants; ++vi)
             for (int mc = 0; mc < kModels; ++mc) {
-                const int n = b->w_cnt[pr][vi][mc];
+                const int n = ls.w_cnt[pr][vi][mc];
                 if (!n) continue;
-                const Work* w = b->d_work + b->w_off[pr][vi][mc];
-                if (pr) launch_collide<float>(w, n, vi, mc, b->d_descs, par, b->d_counter, b->stream);
-                else launch_collide<double>(w, n, vi, mc, b->d_descs, par, b->d_counter, b->stream);
+                const Work* w = b->d_work + ls.w_off[pr][vi][mc];
+                if (pr) launch_collide<float>(w, n, vi, mc, b->d_descs, par, ls.counter, st);
+                else launch_collide<double>(w, n, vi, mc, b->d_descs, par, ls.counter, st);
             }
 }
 
-static void batch_launch_boundary(lbm_batch* b, int par) {
-    const int last = b->b_cnt[1] ? 1 : 0;
+static void batch_launch_boundary(lbm_batch* b, const LaunchSet& ls, int par, cudaStream_t st) {
+    const int last = ls.b_cnt[1] ? 1 : 0;
     for (int pr = 0; pr < 2; ++pr) {
-        if (!b->b_cnt[pr]) continue;
-        long long* ctr = (pr == last) ? b->d_counter : nullptr;
-        if (pr) launch_boundary<float>(b->d_bwork + b->b_off[pr], b->b_cnt[pr], b->d_descs, par, ctr, b->stream);
-        else launch_boundary<double>(b->d_bwork + b->b_off[pr], b->b_cnt[pr], b->d_descs, par, ctr, b->stream);
+        if (!ls.b_cnt[pr]) continue;
+        long long* ctr = (pr == last) ? ls.counter : nullptr;
+        if (pr) launch_boundary<float>(b->d_bwork + ls.b_off[pr], ls.b_cnt[pr], b->d_descs, par, ctr, st);
+        else launch_boundary<double>(b->d_bwork + ls.b_off[pr], ls.b_cnt[pr], b->d_descs, par, ctr, st);
     }
 }
 
-static void batch_launch_step(lbm_batch* b, int par) {
-    batch_launch_collide(b, par);
-    batch_launch_boundary(b, par);
+static void batch_launch_step(lbm_batch* b, const LaunchSet& ls, int par, cudaStream_t st) {
+    batch_launch_collide(b, ls, par, st);
+    batch_launch_boundary(b, ls, par, st);
 }
 
 static lbm_status batch_set_counter(lbm_batch* b) {
-    const long long v = b->steps;
-    CUDA_TRY(cudaMemcpyAsync(b->d_counter, &v, sizeof(v), cudaMemcpyHostToDevice, b->stream));
+    const long long v[3] = {b->steps, b->steps, b->steps};
+    CUDA_TRY(cudaMemcpyAsync(b->d_counter, v, sizeof(v), cudaMemcpyHostToDevice, b->stream));
     return LBM_OK;
+}
+
+// Launch groups of the members listed in `members` (indices into ctxs) into
+// `ls`, appending their work items to `all` and wall items to `ball`.
+static void build_launch_set(lbm_ctx* const* ctxs, const std::vector<int>& members, int shift, LaunchSet& ls,
+                             std::vector<Work>& all, std::vector<BWork>& ball) {
+    std::vector<Work> groups[2][kVariants][kModels];
+    std::vector<BWork> bgroups[2];
+    for (int i : members) {
+        const lbm_ctx* c = ctxs[i];
+        const int pr = is_fp32(c) ? 1 : 0, bi = variant_index(c->bx, c->pair);
+        const int par = (int)(c->steps & 1);
+        auto w = make_work(c->cfg, i, c->bx, c->tile_set ? c->by : std::max(1, batch_rows(c->cfg, c->pair) >> shift),
+                           par, c->steps);
+        auto& grp = groups[pr][bi][launch_model(bi, c->mc)];
+        grp.insert(grp.end(), w.begin(), w.end());
+        auto bw = make_bwork(c->cfg, i, par);
+        bgroups[pr].insert(bgroups[pr].end(), bw.begin(), bw.end());
+    }
+    // longest runs first within each launch, and shorter runs at its end
+    for (int pr = 0; pr < 2; ++pr)
+        for (int bi = 0; bi < kVariants; ++bi)
+            for (int mc = 0; mc < kModels; ++mc) {
+                auto& g = groups[pr][bi][mc];
+                std::stable_sort(g.begin(), g.end(), [](const Work& a, const Work& b) { return a.y1 - a.y0 > b.y1 - b.y0; });
+                if (!g.empty()) split_tail(g, resident_ctas(bi, pr == 1));
+                ls.w_off[pr][bi][mc] = (int)all.size();
+                ls.w_cnt[pr][bi][mc] = (int)g.size();
+                all.insert(all.end(), g.begin(), g.end());
+            }
+    if (bgroups[0].empty() && bgroups[1].empty()) {
+        const lbm_ctx* c = ctxs[members[0]];
+        ensure_tick(bgroups[is_fp32(c) ? 1 : 0], members[0], (int)(c->steps & 1));
+    }
+    for (int pr = 0; pr < 2; ++pr) {
+        ls.b_off[pr] = (int)ball.size();
+        ls.b_cnt[pr] = (int)bgroups[pr].size();
+        ball.insert(ball.end(), bgroups[pr].begin(), bgroups[pr].end());
+    }
 }
 
 lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, int graph_steps, lbm_batch** out) {
     if (!out || !ctxs || n < 1) return fail(LBM_EINVAL, "bad batch arguments");
     *out = nullptr;
     if (graph_steps < 0 || (graph_steps & 1)) return fail(LBM_EINVAL, "graph_steps must be even and >= 0");
+    if (!ctxs[0]) return fail(LBM_EINVAL, "null batch member");
     lbm_batch* b = new lbm_batch();
     b->stream = ctxs[0]->stream;
     std::vector<InstDesc*> descs;
-    std::vector<Work> groups[2][kVariants][kModels];
-    std::vector<BWork> bgroups[2];
     // rows per run of the members whose shape was not set: the batch length,
     // halved for all of them while the batch fills less than the GPU once
     // (each CTA of a member takes 1 / resident_ctas of the GPU)
@@ -3263,45 +3314,45 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, int graph_steps, lbm_ba
         b->ctxs.push_back(c);
         b->models.push_back(c->mc);
         descs.push_back(c->d_desc);
-        const int pr = is_fp32(c) ? 1 : 0, bi = variant_index(c->bx, c->pair);
-        const int par = (int)(c->steps & 1);
-        auto w = make_work(c->cfg, i, c->bx, c->tile_set ? c->by : std::max(1, batch_rows(c->cfg, c->pair) >> shift), par, c->steps);
-        auto& grp = groups[pr][bi][launch_model(bi, c->mc)];
-        grp.insert(grp.end(), w.begin(), w.end());
-        auto bw = make_bwork(c->cfg, i, par);
-        bgroups[pr].insert(bgroups[pr].end(), bw.begin(), bw.end());
     }
     std::vector<Work> all;
-    // longest runs first within each launch, so that short ones fill the tail
-    for (int pr = 0; pr < 2; ++pr)
-        for (int bi = 0; bi < kVariants; ++bi)
-            for (int mc = 0; mc < kModels; ++mc)
-            {
-                std::stable_sort(groups[pr][bi][mc].begin(), groups[pr][bi][mc].end(),
-                                 [](const Work& a, const Work& b) { return a.y1 - a.y0 > b.y1 - b.y0; });
-                if (!groups[pr][bi][mc].empty()) split_tail(groups[pr][bi][mc], resident_ctas(bi, pr == 1));
-            }
-    for (int pr = 0; pr < 2; ++pr)
-        for (int bi = 0; bi < kVariants; ++bi)
-            for (int mc = 0; mc < kModels; ++mc) {
-                b->w_off[pr][bi][mc] = (int)all.size();
-                b->w_cnt[pr][bi][mc] = (int)groups[pr][bi][mc].size();
-                all.insert(all.end(), groups[pr][bi][mc].begin(), groups[pr][bi][mc].end());
-            }
-    if (bgroups[0].empty() && bgroups[1].empty()) ensure_tick(bgroups[is_fp32(ctxs[0]) ? 1 : 0], 0, (int)(ctxs[0]->steps & 1));
     std::vector<BWork> ball;
-    for (int pr = 0; pr < 2; ++pr) {
-        b->b_off[pr] = (int)ball.size();
-        b->b_cnt[pr] = (int)bgroups[pr].size();
-        ball.insert(ball.end(), bgroups[pr].begin(), bgroups[pr].end());
+    std::vector<int> everyone(n);
+    for (int i = 0; i < n; ++i) everyone[i] = i;
+    build_launch_set(ctxs, everyone, shift, b->sets[0], all, ball);
+    // Two halves of about equal node count, for two branches of the graph:
+    // each half's wall pass and the ends of its fused launches overlap the
+    // other half's fused launches, where one branch would leave the GPU to
+    // the latency-bound wall pass and to the last CTAs of each launch.
+    // Worth it only when the batch fills the GPU several times over.
+    long long total = 0;
+    for (int i = 0; i < n; ++i) total += (long long)ctxs[i]->cfg.nx * ctxs[i]->cfg.ny;
+    b->split = graph_steps > 0 && n >= 2 && total >= 4LL * 1024 * 1024;
+    if (b->split) {
+        std::vector<int> order(everyone);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+            return (long long)ctxs[a]->cfg.nx * ctxs[a]->cfg.ny > (long long)ctxs[c]->cfg.nx * ctxs[c]->cfg.ny;
+        });
+        std::vector<int> half[2];
+        long long load[2] = {0, 0};
+        for (int i : order) {
+            const int h = load[0] <= load[1] ? 0 : 1;
+            half[h].push_back(i);
+            load[h] += (long long)ctxs[i]->cfg.nx * ctxs[i]->cfg.ny;
+        }
+        std::sort(half[0].begin(), half[0].end());
+        std::sort(half[1].begin(), half[1].end());
+        build_launch_set(ctxs, half[0], shift, b->sets[1], all, ball);
+        build_launch_set(ctxs, half[1], shift, b->sets[2], all, ball);
     }
     auto bad = [&](const char* m) {
         lbm_batch_destroy(b);
         return fail(LBM_ECUDA, m);
     };
     if (cudaMalloc(&b->d_descs, descs.size() * sizeof(InstDesc*)) != cudaSuccess) return bad("cudaMalloc descs");
-    if (cudaMalloc(&b->d_counter, sizeof(long long)) != cudaSuccess) return bad("cudaMalloc counter");
-    if (cudaMemsetAsync(b->d_counter, 0, sizeof(long long), b->stream) != cudaSuccess) return bad("memset counter");
+    if (cudaMalloc(&b->d_counter, 3 * sizeof(long long)) != cudaSuccess) return bad("cudaMalloc counter");
+    if (cudaMemsetAsync(b->d_counter, 0, 3 * sizeof(long long), b->stream) != cudaSuccess) return bad("memset counter");
+    for (int k = 0; k < 3; ++k) b->sets[k].counter = b->d_counter + k;
     if (!all.empty() && cudaMalloc(&b->d_work, all.size() * sizeof(Work)) != cudaSuccess) return bad("cudaMalloc work");
     if (!ball.empty() && cudaMalloc(&b->d_bwork, ball.size() * sizeof(BWork)) != cudaSuccess) return bad("cudaMalloc bwork");
     if (cudaMemcpyAsync(b->d_descs, descs.data(), descs.size() * sizeof(InstDesc*), cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
@@ -3317,9 +3368,28 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, int graph_steps, lbm_ba
             lbm_batch_destroy(b);
             return fail(LBM_EINVAL, "graph capture needs a non-default stream");
         }
+        if (b->split) {
+            int dev = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess) return bad("cudaGetDevice");
+            if (cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess) return bad("side stream");
+            if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess)
+                return bad("capture events");
+        }
         cudaGraph_t g = nullptr;
         if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return bad("begin capture");
-        for (int s = 0; s < graph_steps; ++s) batch_launch_step(b, s & 1);
+        if (b->split) {
+            cudaEventRecord(b->fork, b->stream);
+            cudaStreamWaitEvent(b->side, b->fork, 0);
+            for (int s = 0; s < graph_steps; ++s) {
+                batch_launch_step(b, b->sets[1], s & 1, b->stream);
+                batch_launch_step(b, b->sets[2], s & 1, b->side);
+            }
+            cudaEventRecord(b->join, b->side);
+            cudaStreamWaitEvent(b->stream, b->join, 0);
+        } else {
+            for (int s = 0; s < graph_steps; ++s) batch_launch_step(b, b->sets[0], s & 1, b->stream);
+        }
         if (cudaStreamEndCapture(b->stream, &g) != cudaSuccess) return bad("end capture");
         cudaError_t e = cudaGraphInstantiate(&b->graph, g, 0);
         cudaGraphDestroy(g);
@@ -3327,6 +3397,36 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, int graph_steps, lbm_ba
     }
     *out = b;
     return LBM_OK;
+}
+
+// Rebuild b in place over a new member list: a new batch is built first, so
+// b is unchanged when that fails.
+static lbm_status batch_rebuild(lbm_batch* b, const std::vector<lbm_ctx*>& members) {
+    lbm_batch* nb = nullptr;
+    lbm_status st = lbm_batch_create(members.data(), (int)members.size(), b->graph_steps, &nb);
+    if (st != LBM_OK) return st;
+    lbm_batch old = std::move(*b);
+    *b = std::move(*nb);
+    *nb = std::move(old);
+    return lbm_batch_destroy(nb);
+}
+
+lbm_status lbm_batch_add(lbm_batch* b, lbm_ctx* c) {
+    if (!b || !c) return fail(LBM_EINVAL, "null batch or context");
+    if (std::find(b->ctxs.begin(), b->ctxs.end(), c) != b->ctxs.end()) return fail(LBM_EINVAL, "already a member");
+    std::vector<lbm_ctx*> m = b->ctxs;
+    m.push_back(c);
+    return batch_rebuild(b, m);
+}
+
+lbm_status lbm_batch_remove(lbm_batch* b, lbm_ctx* c) {
+    if (!b || !c) return fail(LBM_EINVAL, "null batch or context");
+    std::vector<lbm_ctx*> m = b->ctxs;
+    auto it = std::find(m.begin(), m.end(), c);
+    if (it == m.end()) return fail(LBM_EINVAL, "not a member");
+    if (m.size() == 1) return fail(LBM_EINVAL, "a batch keeps at least one member; destroy it instead");
+    m.erase(it);
+    return batch_rebuild(b, m);
 }
 
 lbm_status lbm_batch_step(lbm_batch* b, long nsteps) {
@@ -3343,7 +3443,7 @@ lbm_status lbm_batch_step(lbm_batch* b, long nsteps) {
         if (nsteps % b->graph_steps) return fail(LBM_EINVAL, "nsteps must be a multiple of graph_steps");
         for (long s = 0; s < nsteps; s += b->graph_steps) CUDA_TRY(cudaGraphLaunch(b->graph, b->stream));
     } else {
-        for (long s = 0; s < nsteps; ++s) batch_launch_step(b, (int)((b->steps + s) & 1));
+        for (long s = 0; s < nsteps; ++s) batch_launch_step(b, b->sets[0], (int)((b->steps + s) & 1), b->stream);
         lbm_status st = check_launch();
         if (st != LBM_OK) return st;
     }
@@ -3371,9 +3471,9 @@ lbm_status lbm_batch_step_profiled(lbm_batch* b, long nsteps, double* ms_collide
     for (long s = 0; s < nsteps; ++s) {
         const int par = (int)((b->steps + s) & 1);
         cudaEventRecord(ev[3 * s], b->stream);
-        batch_launch_collide(b, par);
+        batch_launch_collide(b, b->sets[0], par, b->stream);
         cudaEventRecord(ev[3 * s + 1], b->stream);
-        batch_launch_boundary(b, par);
+        batch_launch_boundary(b, b->sets[0], par, b->stream);
         cudaEventRecord(ev[3 * s + 2], b->stream);
     }
     lbm_status st = check_launch();
@@ -3448,6 +3548,9 @@ lbm_status lbm_batch_destroy(lbm_batch* b) {
     if (b->d_diag_out) cudaFree(b->d_diag_out);
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->d_counter) cudaFree(b->d_counter);
+    if (b->side) cudaStreamDestroy(b->side);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->join) cudaEventDestroy(b->join);
     if (b->d_descs) cudaFree(b->d_descs);
     if (b->d_work) cudaFree(b->d_work);
     if (b->d_bwork) cudaFree(b->d_bwork);

@@ -74,7 +74,7 @@ EXPORTS = ("lbm_workspace_bytes", "lbm_create", "lbm_set_eos", "lbm_step", "lbm_
            "lbm_init_macros", "lbm_derived", "lbm_set_tile", "lbm_get_tile", "lbm_step_count", "lbm_destroy",
            "lbm_last_error", "lbm_batch_create", "lbm_batch_step", "lbm_batch_step_profiled",
            "lbm_batch_destroy", "lbm_conserved_sums_static", "lbm_set_rounding", "lbm_copy_state",
-           "lbm_wait_selftest", "lbm_batch_diagnostics")
+           "lbm_wait_selftest", "lbm_batch_diagnostics", "lbm_batch_add", "lbm_batch_remove")
 
 
 def load(path: str | None = None):
@@ -117,6 +117,8 @@ def load(path: str | None = None):
         L.lbm_copy_state.argtypes = [vp, vp]
         L.lbm_wait_selftest.argtypes = [vp, C.c_longlong]
         L.lbm_batch_diagnostics.argtypes = [vp, i, dp, P(C.c_int)]
+        L.lbm_batch_add.argtypes = [vp, vp]
+        L.lbm_batch_remove.argtypes = [vp, vp]
         _lib = L
         return L
 
@@ -313,6 +315,16 @@ class Batch:
         a, b = C.c_double(), C.c_double()
         _check(self.L, self.L.lbm_batch_step_profiled(self.h, int(n), C.byref(a), C.byref(b)))
         return a.value, b.value
+
+    def add(self, lattice):
+        """Append a member (launch tables and graph rebuilt)."""
+        _check(self.L, self.L.lbm_batch_add(self.h, lattice.h))
+        self.lattices.append(lattice)
+
+    def remove(self, lattice):
+        """Drop a member; the others keep their order."""
+        _check(self.L, self.L.lbm_batch_remove(self.h, lattice.h))
+        self.lattices.remove(lattice)
 
     def diagnostics(self, snapshot: bool = False):
         """lbm_diagnostics of every member in one pass: a list of (dict,

@@ -137,7 +137,7 @@ class Server:
     arrivals from overtaking it (None: never)."""
 
     def __init__(self, max_slots: int = 64, mem_fraction: float = 0.85, chunk: int = 1000,
-                 graph_steps: int = 100, stream=None, tile_fn=None, keep_fields: bool = False,
+                 graph_steps: int = 10, stream=None, tile_fn=None, keep_fields: bool = False,
                  fp32_stall: float | None = 1e-4, starvation_s: float | None = None):
         import torch
         self.torch = torch
@@ -312,9 +312,16 @@ class Server:
 
     @property
     def host_overhead(self):
-        """Share of the wall time the device spent not stepping: scheduling,
-        diagnostics, admissions, retirements and batch rebuilds."""
-        return max(0.0, 1.0 - self.gpu_ms * 1e-3 / self.wall) if getattr(self, "wall", 0) else None
+        """Share of the wall time the device waited for the host between two
+        chunks: the results loop, retirements, admissions and the batch
+        rebuild.  (Time with nothing resident, waiting for arrivals, is not
+        counted; device_busy includes it.)"""
+        return self.host_s["between_chunks"] / self.wall if getattr(self, "wall", 0) else None
+
+    @property
+    def device_busy(self):
+        """Share of the wall time the device spent stepping lattices."""
+        return self.gpu_ms * 1e-3 / self.wall if getattr(self, "wall", 0) else None
 
 
 def solve_sequential(req: Request, chunk: int = 1000, keep_fields: bool = False, fp32_stall: float | None = 1e-4):

@@ -66,3 +66,88 @@ def test_batch_diagnostics_reports_an_unstable_member(lbm):
     out = batch.diagnostics()
     assert out[1][1] == lbm.LBM_EUNSTABLE and np.isnan(out[1][0]["mass"])
     batch.close()
+
+
+def test_two_branch_graph_equals_alone(lbm):
+    """A batch of more than 4M nodes replays its graph as two branches, each
+    half of the members on its own (the wall pass of one half overlapping
+    the fused launches of the other); every member still gets the bits it
+    gets stepped alone, FP32 and FP64 members alike, from odd and even
+    starting steps."""
+    import torch
+    stream = torch.cuda.Stream()
+    cfgs = [W.cavity(N=1024, Ra=1e6, eps=0.5, precision=1),
+            W.cavity(N=1024, Ra=3e6, eps=0.3, eos=(W.EOS_CUBIC, (0.05, 0.2)), precision=1),
+            W.cavity(N=768, Ra=1e5, eps=0.6, precision=1),
+            W.cavity(N=640, Ra=1e5, eps=0.4, precision=1),
+            W.cavity(N=300, Ra=1e4, eps=0.5),
+            W.poiseuille(nx=200, ny=190, precision=1)]
+    assert sum(c["nx"] * c["ny"] for c in cfgs) >= 4 * 1024 * 1024
+    alone = [lbm.Lattice(c, stream=stream) for c in cfgs]
+    mixed = [lbm.Lattice(c, stream=stream) for c in cfgs]
+    for a, m in zip(alone[::2], mixed[::2]):
+        a.step(3)
+        m.step(3)
+    batch = lbm.Batch(mixed, graph_steps=10)
+    batch.step(30)
+    for a in alone:
+        a.step(30)
+    stream.synchronize()
+    for a, m in zip(alone, mixed):
+        assert a.steps == m.steps
+        fa, ga = a.get_state()
+        fm, gm = m.get_state()
+        assert np.array_equal(fa, fm) and np.array_equal(ga, gm)
+    # per-step launches after the graph continue from the same step counts
+    batch.step_profiled(4)
+    for a in alone:
+        a.step(4)
+    stream.synchronize()
+    for a, m in zip(alone, mixed):
+        fa, _ = a.get_state()
+        fm, _ = m.get_state()
+        assert np.array_equal(fa, fm)
+    batch.close()
+    for lat in alone + mixed:
+        lat.close()
+
+
+def test_batch_add_remove_keep_bits(lbm):
+    """Members joined with lbm_batch_add or left with lbm_batch_remove get
+    the same bits as lattices stepped alone; the handle stays usable."""
+    import torch
+    stream = torch.cuda.Stream()
+    cfgs = _mix()[:4]
+    alone = [lbm.Lattice(c, stream=stream) for c in cfgs]
+    mixed = [lbm.Lattice(c, stream=stream) for c in cfgs]
+    batch = lbm.Batch(mixed[:2], graph_steps=10)
+    batch.step(20)
+    for a in alone[:2]:
+        a.step(20)
+    mixed[2].step(5)
+    alone[2].step(5)
+    batch.add(mixed[2])                      # joins at an odd step count
+    batch.add(mixed[3])
+    batch.step(30)
+    for a in alone[:4]:
+        a.step(30)
+    batch.remove(mixed[0])
+    assert batch.L.lbm_batch_remove(batch.h, mixed[0].h) == lbm.LBM_EINVAL     # not a member any more
+    assert batch.L.lbm_batch_add(batch.h, mixed[1].h) == lbm.LBM_EINVAL        # already one
+    batch.step(10)
+    for a in alone[1:]:
+        a.step(10)
+    mixed[0].step(10)                         # the removed lattice steps on alone
+    alone[0].step(10)
+    out = batch.diagnostics()
+    assert [st for _, st in out] == [lbm.LBM_OK] * 3
+    stream.synchronize()
+    for a, m in zip(alone, mixed):
+        assert a.steps == m.steps
+        fa, ga = a.get_state()
+        fm, gm = m.get_state()
+        assert np.array_equal(fa, fm) and np.array_equal(ga, gm)
+    for lat in mixed[1:3]:
+        batch.remove(lat)
+    assert batch.L.lbm_batch_remove(batch.h, mixed[3].h) == lbm.LBM_EINVAL     # the last member stays
+    batch.close()
