@@ -224,10 +224,7 @@ const char* lbm_last_error(void);
  * kernel instance, all others the generic one) and one wall-pass launch per
  * precision per step.  A lattice gives the same bits alone or batched.
  * graph_steps > 0 captures that many steps in a CUDA graph that
- * lbm_batch_step replays (nsteps must then be a multiple of graph_steps);
- * a batch of 4,194,304 nodes or more is captured as two branches, each
- * stepping about half of the nodes, so that the wall pass of one half
- * overlaps the fused launches of the other.
+ * lbm_batch_step replays (nsteps must then be a multiple of graph_steps).
  * A member whose EOS class lbm_set_eos changes afterwards makes the batch
  * step fail with LBM_EINVAL: build the batch again. */
 lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, int graph_steps, lbm_batch** out);

@@ -2146,16 +2146,11 @@ struct lbm_batch {
     InstDesc** d_descs = nullptr;
     Work* d_work = nullptr;
     BWork* d_bwork = nullptr;
-    // set 0: every member, for per-step launches; sets 1 and 2: the two
-    // halves of the members, replayed on two branches of the graph
-    LaunchSet sets[3];
-    bool split = false;
+    LaunchSet set;                   // every member's launches of one time step
     long steps = 0;
     int graph_steps = 0;
     cudaGraphExec_t graph = nullptr;
-    cudaStream_t side = nullptr;     // second capture branch
-    cudaEvent_t fork = nullptr, join = nullptr;
-    long long* d_counter = nullptr;  // three step counters, one per launch set, advanced on the device
+    long long* d_counter = nullptr;  // the batch's step counter, advanced on the device
     DiagJob* d_jobs = nullptr;       // lbm_batch_diagnostics: one job per member, FP32 members first
     double* d_diag_out = nullptr;    // [member][kDiagSlots + 1] sums and status word
     std::vector<int> diag_order;     // members in job order
@@ -3236,8 +3231,8 @@ static void batch_launch_step(lbm_batch* b, const LaunchSet& ls, int par, cudaSt
 }
 
 static lbm_status batch_set_counter(lbm_batch* b) {
-    const long long v[3] = {b->steps, b->steps, b->steps};
-    CUDA_TRY(cudaMemcpyAsync(b->d_counter, v, sizeof(v), cudaMemcpyHostToDevice, b->stream));
+    const long long v = b->steps;
+    CUDA_TRY(cudaMemcpyAsync(b->d_counter, &v, sizeof(v), cudaMemcpyHostToDevice, b->stream));
     return LBM_OK;
 }
 
@@ -3319,40 +3314,15 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, int graph_steps, lbm_ba
     std::vector<BWork> ball;
     std::vector<int> everyone(n);
     for (int i = 0; i < n; ++i) everyone[i] = i;
-    build_launch_set(ctxs, everyone, shift, b->sets[0], all, ball);
-    // Two halves of about equal node count, for two branches of the graph:
-    // each half's wall pass and the ends of its fused launches overlap the
-    // other half's fused launches, where one branch would leave the GPU to
-    // the latency-bound wall pass and to the last CTAs of each launch.
-    // Worth it only when the batch fills the GPU several times over.
-    long long total = 0;
-    for (int i = 0; i < n; ++i) total += (long long)ctxs[i]->cfg.nx * ctxs[i]->cfg.ny;
-    b->split = graph_steps > 0 && n >= 2 && total >= 4LL * 1024 * 1024;
-    if (b->split) {
-        std::vector<int> order(everyone);
-        std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
-            return (long long)ctxs[a]->cfg.nx * ctxs[a]->cfg.ny > (long long)ctxs[c]->cfg.nx * ctxs[c]->cfg.ny;
-        });
-        std::vector<int> half[2];
-        long long load[2] = {0, 0};
-        for (int i : order) {
-            const int h = load[0] <= load[1] ? 0 : 1;
-            half[h].push_back(i);
-            load[h] += (long long)ctxs[i]->cfg.nx * ctxs[i]->cfg.ny;
-        }
-        std::sort(half[0].begin(), half[0].end());
-        std::sort(half[1].begin(), half[1].end());
-        build_launch_set(ctxs, half[0], shift, b->sets[1], all, ball);
-        build_launch_set(ctxs, half[1], shift, b->sets[2], all, ball);
-    }
+    build_launch_set(ctxs, everyone, shift, b->set, all, ball);
     auto bad = [&](const char* m) {
         lbm_batch_destroy(b);
         return fail(LBM_ECUDA, m);
     };
     if (cudaMalloc(&b->d_descs, descs.size() * sizeof(InstDesc*)) != cudaSuccess) return bad("cudaMalloc descs");
-    if (cudaMalloc(&b->d_counter, 3 * sizeof(long long)) != cudaSuccess) return bad("cudaMalloc counter");
-    if (cudaMemsetAsync(b->d_counter, 0, 3 * sizeof(long long), b->stream) != cudaSuccess) return bad("memset counter");
-    for (int k = 0; k < 3; ++k) b->sets[k].counter = b->d_counter + k;
+    if (cudaMalloc(&b->d_counter, sizeof(long long)) != cudaSuccess) return bad("cudaMalloc counter");
+    if (cudaMemsetAsync(b->d_counter, 0, sizeof(long long), b->stream) != cudaSuccess) return bad("memset counter");
+    b->set.counter = b->d_counter;
     if (!all.empty() && cudaMalloc(&b->d_work, all.size() * sizeof(Work)) != cudaSuccess) return bad("cudaMalloc work");
     if (!ball.empty() && cudaMalloc(&b->d_bwork, ball.size() * sizeof(BWork)) != cudaSuccess) return bad("cudaMalloc bwork");
     if (cudaMemcpyAsync(b->d_descs, descs.data(), descs.size() * sizeof(InstDesc*), cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
@@ -3368,28 +3338,9 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, int graph_steps, lbm_ba
             lbm_batch_destroy(b);
             return fail(LBM_EINVAL, "graph capture needs a non-default stream");
         }
-        if (b->split) {
-            int dev = 0;
-            if (cudaGetDevice(&dev) != cudaSuccess) return bad("cudaGetDevice");
-            if (cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess) return bad("side stream");
-            if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
-                cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess)
-                return bad("capture events");
-        }
         cudaGraph_t g = nullptr;
         if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return bad("begin capture");
-        if (b->split) {
-            cudaEventRecord(b->fork, b->stream);
-            cudaStreamWaitEvent(b->side, b->fork, 0);
-            for (int s = 0; s < graph_steps; ++s) {
-                batch_launch_step(b, b->sets[1], s & 1, b->stream);
-                batch_launch_step(b, b->sets[2], s & 1, b->side);
-            }
-            cudaEventRecord(b->join, b->side);
-            cudaStreamWaitEvent(b->stream, b->join, 0);
-        } else {
-            for (int s = 0; s < graph_steps; ++s) batch_launch_step(b, b->sets[0], s & 1, b->stream);
-        }
+        for (int s = 0; s < graph_steps; ++s) batch_launch_step(b, b->set, s & 1, b->stream);
         if (cudaStreamEndCapture(b->stream, &g) != cudaSuccess) return bad("end capture");
         cudaError_t e = cudaGraphInstantiate(&b->graph, g, 0);
         cudaGraphDestroy(g);
@@ -3443,7 +3394,7 @@ lbm_status lbm_batch_step(lbm_batch* b, long nsteps) {
         if (nsteps % b->graph_steps) return fail(LBM_EINVAL, "nsteps must be a multiple of graph_steps");
         for (long s = 0; s < nsteps; s += b->graph_steps) CUDA_TRY(cudaGraphLaunch(b->graph, b->stream));
     } else {
-        for (long s = 0; s < nsteps; ++s) batch_launch_step(b, b->sets[0], (int)((b->steps + s) & 1), b->stream);
+        for (long s = 0; s < nsteps; ++s) batch_launch_step(b, b->set, (int)((b->steps + s) & 1), b->stream);
         lbm_status st = check_launch();
         if (st != LBM_OK) return st;
     }
@@ -3471,9 +3422,9 @@ lbm_status lbm_batch_step_profiled(lbm_batch* b, long nsteps, double* ms_collide
     for (long s = 0; s < nsteps; ++s) {
         const int par = (int)((b->steps + s) & 1);
         cudaEventRecord(ev[3 * s], b->stream);
-        batch_launch_collide(b, b->sets[0], par, b->stream);
+        batch_launch_collide(b, b->set, par, b->stream);
         cudaEventRecord(ev[3 * s + 1], b->stream);
-        batch_launch_boundary(b, b->sets[0], par, b->stream);
+        batch_launch_boundary(b, b->set, par, b->stream);
         cudaEventRecord(ev[3 * s + 2], b->stream);
     }
     lbm_status st = check_launch();
@@ -3548,9 +3499,6 @@ lbm_status lbm_batch_destroy(lbm_batch* b) {
     if (b->d_diag_out) cudaFree(b->d_diag_out);
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->d_counter) cudaFree(b->d_counter);
-    if (b->side) cudaStreamDestroy(b->side);
-    if (b->fork) cudaEventDestroy(b->fork);
-    if (b->join) cudaEventDestroy(b->join);
     if (b->d_descs) cudaFree(b->d_descs);
     if (b->d_work) cudaFree(b->d_work);
     if (b->d_bwork) cudaFree(b->d_bwork);

@@ -68,21 +68,19 @@ def test_batch_diagnostics_reports_an_unstable_member(lbm):
     batch.close()
 
 
-def test_two_branch_graph_equals_alone(lbm):
-    """A batch of more than 4M nodes replays its graph as two branches, each
-    half of the members on its own (the wall pass of one half overlapping
-    the fused launches of the other); every member still gets the bits it
-    gets stepped alone, FP32 and FP64 members alike, from odd and even
-    starting steps."""
+def test_graph_batch_of_large_lattices_equals_alone(lbm):
+    """Lattices large enough for the batch's shortened last runs and its
+    cavity-model launch group, replayed from a graph: every member gets the
+    bits it gets stepped alone, FP32 and FP64 members alike, from odd and
+    even starting steps, and per-step launches after the graph continue
+    from the same step counts."""
     import torch
     stream = torch.cuda.Stream()
     cfgs = [W.cavity(N=1024, Ra=1e6, eps=0.5, precision=1),
             W.cavity(N=1024, Ra=3e6, eps=0.3, eos=(W.EOS_CUBIC, (0.05, 0.2)), precision=1),
             W.cavity(N=768, Ra=1e5, eps=0.6, precision=1),
-            W.cavity(N=640, Ra=1e5, eps=0.4, precision=1),
             W.cavity(N=300, Ra=1e4, eps=0.5),
             W.poiseuille(nx=200, ny=190, precision=1)]
-    assert sum(c["nx"] * c["ny"] for c in cfgs) >= 4 * 1024 * 1024
     alone = [lbm.Lattice(c, stream=stream) for c in cfgs]
     mixed = [lbm.Lattice(c, stream=stream) for c in cfgs]
     for a, m in zip(alone[::2], mixed[::2]):
