@@ -28,6 +28,8 @@ Fields of the JSON line (rank 0):
   serving   a Poisson stream of cavity and channel solves to residual 1e-7
             through the continuous-batching server; a subset solved four
             ways (batched or one at a time, FP32 then FP64 or FP64 only)
+  fp64_path the FP64-storage kernels on a 2048^2 cavity, native FP64 and
+            double-float arithmetic, against the probed arithmetic rates
   cpu_baseline  the FP64 CPU oracle on a bounded sample (rank 0, N = 1)
 `--impl reference` times that oracle alone (the reference arm).
 Multi-GPU: instances are independent, so each rank advances its own copy of
@@ -102,7 +104,7 @@ def workload(name, precision):
 
 
 KERNEL_OF_PAIR = {0: "k_collide_stream", 1: "k_collide_pair", 2: "k_collide_pair", 3: "k_collide_stream",
-                  4: "k_collide_warp", 5: "k_collide_warp2"}
+                  4: "k_collide_warp", 5: "k_collide_warp2", 6: "k_collide_stream"}
 KERNEL_SOURCES = ("lbm_gb300.cu", "lbm_node.cuh", "lbm_f2.cuh")
 
 
@@ -320,7 +322,8 @@ def steady_cavity512(tol=1e-8):
     from paper_1809_08683_gb300 import autotune, serve
     cfg = W.cavity(N=512, Ra=1e6, eps=0.6, precision=1)
     req = serve.Request(rid=0, cfg=cfg, tol=tol, max_steps=3_000_000)
-    srv = serve.Server(max_slots=1, chunk=1000, graph_steps=1000, tile_fn=lambda c: autotune.tune(c, steps=10))
+    srv = serve.Server(max_slots=1, chunk=1000, graph_steps=1000, tile_fn=lambda c: autotune.tune(c, steps=10),
+                       finish_tile_fn=None)
     for prec in (1, 0):                 # tune outside the timed solve
         autotune.tune(dict(cfg, precision=prec), steps=10)
     srv.run([req], realtime=False)
@@ -372,6 +375,43 @@ def table2_run(Ra, steps, every=20_000):
             "table2": {"nu": nu_ref, "pstar": p_ref}, "nu_vs_table2": nu / nu_ref - 1.0,
             "pstar_vs_table2": ps / p_ref - 1.0, "wall_s": wall,
             "series": [[r[0], round(r[1], 5), round(r[2], 5), round(r[3], 6)] for r in rec[::5]]}
+
+
+# FP64 operations per node update of the heated-cavity model, counted by
+# instantiating the node templates with an operation-counting number type:
+# 308 additions, 289 multiplications, 10 divisions, 1 square root, and
+# about 36 for the gradient stencil.
+FP64_OPS_PER_NODE = 644
+
+
+def fp64_path(n_side=2048, steps=10):
+    """The FP64-storage kernels on an n_side^2 heated cavity (Ra = 1e8,
+    eps = 0.6): per-step fused-kernel time in native FP64 (block strips,
+    pair 0) and in double-float arithmetic (pair 6), against the device's
+    probed FP64 and double-float multiply-add rates, which bound them."""
+    import torch
+    from paper_1809_08683_gb300 import lbm
+    st = torch.cuda.Stream()
+    rates = lbm.peak_rates(st)
+    cfg = W.cavity(N=n_side, Ra=1e8, eps=0.6, precision=0)
+    out = {"workload": f"cavity_{n_side}x{n_side}_Ra1e8_eps0.6_fp64", "rates": rates,
+           "ops_per_node": FP64_OPS_PER_NODE}
+    with torch.cuda.stream(st):
+        lat = lbm.Lattice(cfg, stream=st)
+    for name, tile in (("native_fp64", (128, 8, 0)), ("double_float", (128, 8, 6))):
+        lat.set_tile(*tile)
+        b = lbm.Batch([lat], graph_steps=0)
+        b.step_profiled(3)
+        ms, _ = b.step_profiled(steps)
+        b.close()
+        mlups = n_side * n_side * steps / (ms * 1e-3) / 1e6
+        out[name] = {"tile": list(tile), "fused_ms_per_step": ms / steps, "mlups": mlups,
+                     "counted_gflops": mlups * FP64_OPS_PER_NODE / 1e3}
+    lat.close()
+    out["double_float_speedup"] = out["native_fp64"]["fused_ms_per_step"] / out["double_float"]["fused_ms_per_step"]
+    # FP64 FMA counts two operations
+    out["native_fp64"]["frac_of_fp64_peak"] = out["native_fp64"]["counted_gflops"] * 1e9 / (2 * rates["fp64_fma_per_s"])
+    return out
 
 
 def steady_sweep_subset(tol=1e-5, max_side=256):
@@ -575,6 +615,9 @@ def main():
     lats, batch = [], None
     torch.cuda.empty_cache()
 
+    fp64 = None
+    if rank == 0 and not args.no_steady and args.workload == "batched_sweep":
+        fp64 = fp64_path()
     steady = None
     if rank == 0 and not args.no_steady and args.workload == "batched_sweep":
         steady = {"cavity512": steady_cavity512(), "sweep_subset": steady_sweep_subset()}
@@ -597,7 +640,7 @@ def main():
                          "avg_launch_ms": avg_collide_ms, "wall_pass_ms_per_step": t_wall / psteps},
             "autotune": tuned, "ungraphed": ungraphed,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches, "clocks": clocks,
-            "time_to_steady": steady, "serving": serving,
+            "time_to_steady": steady, "fp64_path": fp64, "serving": serving,
         }
         print(json.dumps(out))
     if world > 1:

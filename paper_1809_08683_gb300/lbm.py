@@ -74,7 +74,8 @@ EXPORTS = ("lbm_workspace_bytes", "lbm_create", "lbm_set_eos", "lbm_step", "lbm_
            "lbm_init_macros", "lbm_derived", "lbm_set_tile", "lbm_get_tile", "lbm_step_count", "lbm_destroy",
            "lbm_last_error", "lbm_batch_create", "lbm_batch_step", "lbm_batch_step_profiled",
            "lbm_batch_destroy", "lbm_conserved_sums_static", "lbm_set_rounding", "lbm_copy_state",
-           "lbm_wait_selftest", "lbm_batch_diagnostics", "lbm_batch_add", "lbm_batch_remove")
+           "lbm_wait_selftest", "lbm_batch_diagnostics", "lbm_batch_add", "lbm_batch_remove",
+           "lbm_peak_rates")
 
 
 def load(path: str | None = None):
@@ -118,6 +119,7 @@ def load(path: str | None = None):
         L.lbm_wait_selftest.argtypes = [vp, C.c_longlong]
         L.lbm_batch_diagnostics.argtypes = [vp, i, dp, P(C.c_int)]
         L.lbm_batch_add.argtypes = [vp, vp]
+        L.lbm_peak_rates.argtypes = [vp, dp]
         L.lbm_batch_remove.argtypes = [vp, vp]
         _lib = L
         return L
@@ -157,6 +159,15 @@ def make_config(cfg: dict) -> Config:
         k.wall[s].u[0], k.wall[s].u[1] = u[0], u[1]
         k.wall[s].T = w.get("T", cfg["T0"])
     return k
+
+
+def peak_rates(stream=None) -> dict:
+    """FP64 FMA, FP32 FMA and double-float multiply-add rates per second of
+    the current device (lbm_peak_rates)."""
+    L = load()
+    a = np.empty(3)
+    _check(L, L.lbm_peak_rates(C.c_void_p(stream.cuda_stream if stream is not None else 0), _ptr(a)))
+    return {"fp64_fma_per_s": float(a[0]), "fp32_fma_per_s": float(a[1]), "ff64_madd_per_s": float(a[2])}
 
 
 def workspace_bytes(cfg: dict) -> int:

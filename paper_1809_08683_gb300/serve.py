@@ -88,6 +88,13 @@ def _fp64(cfg):
     return c
 
 
+def finish_tile(cfg):
+    """Launch shape of an FP64 finish: block strips in double-float
+    arithmetic (pair 6), 32 columns for narrow lattices, 128 otherwise, with
+    the FP64 default run length."""
+    return (128 if int(cfg["nx"]) > 64 else 32, max(1, min(8, int(cfg["ny"]) // 128)), 6)
+
+
 class _Timer:
     """Device time between start() and stop() on the serving stream (CUDA
     events); wall-clock time when the stream is not a CUDA stream."""
@@ -134,11 +141,14 @@ class Server:
     later is seen.  fp32_stall: the residual below which an FP32 solve that
     stops improving moves to FP64 (fp32_stalled); None keeps FP32 to the
     end.  starvation_s: a request that has waited this long stops later
-    arrivals from overtaking it (None: never)."""
+    arrivals from overtaking it (None: never).  finish_tile_fn: launch shape
+    of the FP64 lattice an FP32 solve finishes in (default: double-float
+    block strips, finish_tile; None: the FP64 default)."""
 
     def __init__(self, max_slots: int = 64, mem_fraction: float = 0.85, chunk: int = 1000,
                  graph_steps: int = 10, stream=None, tile_fn=None, keep_fields: bool = False,
-                 fp32_stall: float | None = 1e-4, starvation_s: float | None = None):
+                 fp32_stall: float | None = 1e-4, starvation_s: float | None = None,
+                 finish_tile_fn=finish_tile):
         import torch
         self.torch = torch
         self.max_slots = max_slots
@@ -149,6 +159,7 @@ class Server:
         self.tile_fn = tile_fn
         self.keep_fields = keep_fields
         self.fp32_stall = fp32_stall
+        self.finish_tile_fn = finish_tile_fn
         self.starvation_s = starvation_s
         free, total = torch.cuda.mem_get_info()
         self.total = total
@@ -304,6 +315,8 @@ class Server:
         if not self._fits(nbytes):
             return False
         lat = self._new_lattice(cfg)
+        if self.finish_tile_fn is not None:
+            lat.set_tile(*self.finish_tile_fn(cfg))
         lat.copy_state_from(slot.lat)
         slot.lat.close()
         self.in_use += nbytes - slot.bytes
@@ -324,7 +337,8 @@ class Server:
         return self.gpu_ms * 1e-3 / self.wall if getattr(self, "wall", 0) else None
 
 
-def solve_sequential(req: Request, chunk: int = 1000, keep_fields: bool = False, fp32_stall: float | None = 1e-4):
+def solve_sequential(req: Request, chunk: int = 1000, keep_fields: bool = False, fp32_stall: float | None = 1e-4,
+                     finish_tile_fn=finish_tile):
     """Plain per-request solve: the lattice alone, per-step launches, the
     same residual schedule (and the same move from FP32 to FP64 once FP32
     stalls).  The baseline the batched server is compared to."""
@@ -347,6 +361,8 @@ def solve_sequential(req: Request, chunk: int = 1000, keep_fields: bool = False,
             break
         if int(lat.cfg.get("precision", 0)) == lbm.FP32_DEV and fp32_stalled(req.history, fp32_stall):
             lat64 = lbm.Lattice(_fp64(lat.cfg))
+            if finish_tile_fn is not None:
+                lat64.set_tile(*finish_tile_fn(lat64.cfg))
             lat64.copy_state_from(lat)
             lat.close()
             lat = lat64
