@@ -28,8 +28,8 @@ Fields of the JSON line (rank 0):
   serving   a Poisson stream of cavity and channel solves to residual 1e-7
             through the continuous-batching server; a subset solved four
             ways (batched or one at a time, FP32 then FP64 or FP64 only)
-  fp64_path the FP64-storage kernels on a 2048^2 cavity, native FP64 and
-            double-float arithmetic, against the probed arithmetic rates
+  fp64_path the FP64-storage kernel on a 2048^2 cavity against the probed
+            FP64 FMA rate
   cpu_baseline  the FP64 CPU oracle on a bounded sample (rank 0, N = 1)
 `--impl reference` times that oracle alone (the reference arm).
 Multi-GPU: instances are independent, so each rank advances its own copy of
@@ -104,7 +104,7 @@ def workload(name, precision):
 
 
 KERNEL_OF_PAIR = {0: "k_collide_stream", 1: "k_collide_pair", 2: "k_collide_pair", 3: "k_collide_stream",
-                  4: "k_collide_warp", 5: "k_collide_warp2", 6: "k_collide_stream"}
+                  4: "k_collide_warp", 5: "k_collide_warp2"}
 KERNEL_SOURCES = ("lbm_gb300.cu", "lbm_node.cuh", "lbm_f2.cuh")
 
 
@@ -322,8 +322,7 @@ def steady_cavity512(tol=1e-8):
     from paper_1809_08683_gb300 import autotune, serve
     cfg = W.cavity(N=512, Ra=1e6, eps=0.6, precision=1)
     req = serve.Request(rid=0, cfg=cfg, tol=tol, max_steps=3_000_000)
-    srv = serve.Server(max_slots=1, chunk=1000, graph_steps=1000, tile_fn=lambda c: autotune.tune(c, steps=10),
-                       finish_tile_fn=None)
+    srv = serve.Server(max_slots=1, chunk=1000, graph_steps=1000, tile_fn=lambda c: autotune.tune(c, steps=10))
     for prec in (1, 0):                 # tune outside the timed solve
         autotune.tune(dict(cfg, precision=prec), steps=10)
     srv.run([req], realtime=False)
@@ -385,10 +384,9 @@ FP64_OPS_PER_NODE = 644
 
 
 def fp64_path(n_side=2048, steps=10):
-    """The FP64-storage kernels on an n_side^2 heated cavity (Ra = 1e8,
-    eps = 0.6): per-step fused-kernel time in native FP64 (block strips,
-    pair 0) and in double-float arithmetic (pair 6), against the device's
-    probed FP64 and double-float multiply-add rates, which bound them."""
+    """The FP64-storage fused kernel on an n_side^2 heated cavity (Ra =
+    1e8, eps = 0.6, block strips): per-step time and counted FP64 operation
+    rate against the device's probed FP64 FMA rate, which bounds it."""
     import torch
     from paper_1809_08683_gb300 import lbm
     st = torch.cuda.Stream()
@@ -398,7 +396,7 @@ def fp64_path(n_side=2048, steps=10):
            "ops_per_node": FP64_OPS_PER_NODE}
     with torch.cuda.stream(st):
         lat = lbm.Lattice(cfg, stream=st)
-    for name, tile in (("native_fp64", (128, 8, 0)), ("double_float", (128, 8, 6))):
+    for name, tile in (("native_fp64", (128, 8, 0)),):
         lat.set_tile(*tile)
         b = lbm.Batch([lat], graph_steps=0)
         b.step_profiled(3)
@@ -408,7 +406,6 @@ def fp64_path(n_side=2048, steps=10):
         out[name] = {"tile": list(tile), "fused_ms_per_step": ms / steps, "mlups": mlups,
                      "counted_gflops": mlups * FP64_OPS_PER_NODE / 1e3}
     lat.close()
-    out["double_float_speedup"] = out["native_fp64"]["fused_ms_per_step"] / out["double_float"]["fused_ms_per_step"]
     # FP64 FMA counts two operations
     out["native_fp64"]["frac_of_fp64_peak"] = out["native_fp64"]["counted_gflops"] * 1e9 / (2 * rates["fp64_fma_per_s"])
     return out

@@ -184,7 +184,8 @@ lbm_status lbm_wait_selftest(lbm_ctx* ctx, long long limit_cycles);
 /* Arithmetic rates of the current device, for the roofline of the FP64
  * path, which the FP64 pipe bounds: out3[0] FP64 fused multiply-adds per
  * second, out3[1] FP32 fused multiply-adds per second, out3[2]
- * double-float multiply-adds (pair 6 arithmetic) per second, each the best
+ * double-float multiply-adds (pairs of FP32 numbers carrying about 48
+ * significant bits) per second, each the best
  * of three launches of dependent chains over the whole device.  Allocates
  * and frees a small device buffer; synchronises the stream (NULL = legacy
  * default stream).  The paper has no counterpart. */
@@ -201,11 +202,7 @@ lbm_status lbm_peak_rates(void* cuda_stream, double* out3);
  * and never synchronise with one another, bx = 30, 60 or 120 (1, 2 or 4
  * warps per CTA), any precision.  pair = 5 (FP32 storage only): warp
  * strips of 60 columns, two neighbouring nodes per lane in packed FP32,
- * bx = 60, 120 or 240.  pair = 6 (FP64 storage only): block strips, bx =
- * 32 or 128, running the node arithmetic in double-float (pairs of FP32
- * numbers, about 48 significant bits) instead of FP64 instructions, which
- * GB300 executes at a small fraction of the FP32 rate; its results agree
- * with pair 0 to that precision.  pair = 0 and pair = 4 shapes of any width give
+ * bx = 60, 120 or 240.  pair = 0 and pair = 4 shapes of any width give
  * identical results; pairs 1-3 and 5 agree with them to FP32 rounding (their
  * arithmetic is contracted differently).  (bx, by, pair) = (0, 0, 0)
  * restores the default shape, which batches may then shorten.

@@ -55,17 +55,13 @@ def _store(d):
 PAIR_BX_CANDIDATES = (64, 128, 256)
 WARP_BX_CANDIDATES = (30, 60, 120)
 WARP2_BX_CANDIDATES = (60, 120, 240)
-FF_BX_CANDIDATES = (32, 128)    # FP64 storage, double-float arithmetic
 
 
 def candidates(cfg: dict):
     """(bx, by, pair) shapes worth timing for this lattice: one node per
-    thread in block strips or warp strips for every precision, block strips
-    in double-float arithmetic for FP64 storage, two nodes per thread for
-    FP32 storage."""
+    thread in block strips or warp strips for every precision, two nodes per
+    thread for FP32 storage."""
     shapes = [(bx, 0) for bx in BX_CANDIDATES] + [(bx, 4) for bx in WARP_BX_CANDIDATES]
-    if int(cfg.get("precision", 0)) == 0:
-        shapes += [(bx, 6) for bx in FF_BX_CANDIDATES]
     if int(cfg.get("precision", 0)) == 1:
         shapes += [(bx, 3) for bx in BX_CANDIDATES]
         shapes += [(bx, pr) for bx in PAIR_BX_CANDIDATES for pr in (1, 2)]

@@ -166,48 +166,15 @@ struct AddDither {
         f = f + df;
         g = g + dg;
     }
-    __device__ __forceinline__ void operator()(ff64& f, ff64 df, ff64& g, ff64 dg) const {
-        f = f + df;
-        g = g + dg;
-    }
 };
 
-__device__ __forceinline__ float dither_scale(float v) { return v; }
-__device__ __forceinline__ float dither_scale(double v) { return (float)v; }
-__device__ __forceinline__ float dither_scale(const ff64& v) { return v.hi; }
-
-// Parameters in the arithmetic type A from the descriptor's FP64 set.
-__device__ void params_to(Params<ff64>& b, const Params<double>& a) {
-#define CV(f) b.f = ff64(a.f)
-    CV(rho0); CV(T0); CV(E0); CV(Cv); CV(inv_Cv); CV(Rg); CV(eos_a); CV(eos_b); CV(p0); CV(rho0E0_p0);
-    CV(rho0Cp0); CV(mu0); CV(inv_T0); CV(visc_S); CV(lam_fac); CV(tj_fac); CV(e_fac); CV(alpha1);
-    CV(beta1); CV(alpha2); CV(beta2); CV(kk); CV(hh); CV(bb); CV(gamma1); CV(gamma2); CV(cR11);
-    CV(cR17); CV(cR18); CV(cR71); CV(cR77); CV(cR81); CV(cR88); CV(Fx); CV(Fy); CV(cs_b0); CV(dither);
-#undef CV
-    b.eos = a.eos;
-    b.visc = a.visc;
-    b.force_mode = a.force_mode;
-    b.corrections = a.corrections;
-}
-
 // rho' and p' of node (xx, yy) read straight from a buffer.
-// Conversions between the storage type R of a DF buffer and the type A
-// the node arithmetic runs in (the same type except for FP64 storage with
-// double-float arithmetic).
-template <typename A, typename R>
-__device__ __forceinline__ A from_storage(R v) { return A(v); }
-template <typename R, typename A>
-__device__ __forceinline__ R to_storage(const A& v) { return R(v); }
-
-template <int MC = lbm::MODEL_ANY, typename A, typename R>
-__device__ void rho_p_at(const Params<A>& P, const R* __restrict__ src, long long plane, int pitch,
-                         int xx, int yy, A& rd, A& pd) {
-    R w[18];
-    load18(src, plane, (long long)yy * pitch + xx, w);
-    A v[18];
-#pragma unroll
-    for (int q = 0; q < 18; ++q) v[q] = from_storage<A>(w[q]);
-    Mac<A> m;
+template <int MC = lbm::MODEL_ANY, typename R>
+__device__ void rho_p_at(const Params<R>& P, const R* __restrict__ src, long long plane, int pitch,
+                         int xx, int yy, R& rd, R& pd) {
+    R v[18];
+    load18(src, plane, (long long)yy * pitch + xx, v);
+    Mac<R> m;
     node_macros<MC>(P, v, m);
     rd = m.rho_d;
     pd = m.p_d;
@@ -480,29 +447,25 @@ struct FusedTraits {
 // KEEP = true carries each thread's macros from the row pass to the
 // collision; KEEP = false recomputes them from the staged DFs, trading about
 // 50 instructions per node for fewer registers and more resident warps.
-// A is the arithmetic type: R itself, or double-float (ff64) for FP64
-// storage (pair 6), which runs the same node arithmetic in FP32 instructions.
-template <typename R, int BX, int S, bool KEEP = true, int MC = lbm::MODEL_ANY, typename A = R>
+template <typename R, int BX, int S, bool KEEP = true, int MC = lbm::MODEL_ANY>
 __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTraits<R, BX>::MINB_LEAN)
     k_collide_stream(const Work* __restrict__ work, InstDesc* const* __restrict__ descs, int step_par,
                      const long long* __restrict__ counter) {
     using L = FusedSmem<R, BX, S>;
-    static_assert(sizeof(A) == sizeof(R), "the shared-memory layout assumes arithmetic and storage of one size");
     constexpr int E = L::E, W = L::W;
     constexpr size_t SST = L::stage_bytes / sizeof(R);  // elements from one stage to the next
     extern __shared__ __align__(128) unsigned char smem[];
     R* stage = reinterpret_cast<R*>(smem);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::off_bars);
-    Params<A>& P = *reinterpret_cast<Params<A>*>(smem + L::off_params);
-    RhoP<A>(*s_rp)[BX + 2] = reinterpret_cast<RhoP<A>(*)[BX + 2]>(smem + L::off_ring);
+    Params<R>& P = *reinterpret_cast<Params<R>*>(smem + L::off_params);
+    RhoP<R>(*s_rp)[BX + 2] = reinterpret_cast<RhoP<R>(*)[BX + 2]>(smem + L::off_ring);
     __shared__ int s_abort;
 
     const Work w = work[blockIdx.x];
     const InstDesc* D = descs[w.inst];
     if (smem_misaligned(smem, D->status)) return;
+    load_params(&P, &dparams<R>(D));
     const int tid = threadIdx.x;
-    if constexpr (std::is_same<A, R>::value) load_params(&P, &dparams<R>(D));
-    else if (tid == 0) params_to(P, D->pd);
     if (tid == 0) {
         for (int k = 0; k < S; ++k) mbar_init(&bars[k], 1);
         fence_mbar_init();
@@ -516,7 +479,7 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
     unsigned int* status = D->status;
     const uint32_t step_hash = mix32((uint32_t)(w.step0 + *counter) * 0x9e3779b1u + 0x632be5abu);
     __syncthreads();
-    const float dscale = dither_scale(P.dither);
+    const float dscale = (float)P.dither;
 
     const int x = w.x0 + tid;
     const bool active = x < nx;
@@ -585,7 +548,7 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
 
     // wait for logical row l and put its rho', p' into ring slot l % 4;
     // active threads also return their own node's macros in m
-    auto row_macros = [&](int l, MacC<A>& mk) -> bool {
+    auto row_macros = [&](int l, MacC<R>& mk) -> bool {
         const int s = l % S;
         if (!mbar_wait(&bars[s], (uint32_t)((l / S) & 1))) {
             atomicOr(status, 2u);
@@ -596,13 +559,13 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
         const R* st = stage + (size_t)s * SST;
         const int slot = l & 3;
         if (active) {
-            A v[18];
+            R v[18];
 #pragma unroll
-            for (int q = 0; q < 18; ++q) v[q] = from_storage<A>(st[q * W + E + tid]);
-            Mac<A> m;
+            for (int q = 0; q < 18; ++q) v[q] = st[q * W + E + tid];
+            Mac<R> m;
             node_macros<MC>(P, v, m);
             compress(m, mk);
-            s_rp[slot][c] = RhoP<A>{m.rho_d, m.p_d};
+            s_rp[slot][c] = RhoP<R>{m.rho_d, m.p_d};
         }
         // the two halo columns: two adjacent lanes of one warp run the same
         // instruction stream on their own chunk, in warp 1 (not the warp
@@ -612,18 +575,18 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
         if (hl || hr) {
             const int off = hl ? (xhl - xcl) : (E + BX + (xhr - xcr));
             const int col = hl ? 0 : tlast + 2;
-            A v[18];
+            R v[18];
 #pragma unroll
-            for (int q = 0; q < 18; ++q) v[q] = from_storage<A>(st[q * W + off]);
-            Mac<A> h;
+            for (int q = 0; q < 18; ++q) v[q] = st[q * W + off];
+            Mac<R> h;
             node_macros<MC>(P, v, h);
-            s_rp[slot][col] = RhoP<A>{h.rho_d, h.p_d};
+            s_rp[slot][col] = RhoP<R>{h.rho_d, h.p_d};
         }
         return true;
     };
 
     for (int l = 0; l < S; ++l) issue(l);
-    MacC<A> mc, mn;
+    MacC<R> mc, mn;
     if (phys(0) >= 0) row_macros(0, mn);
     row_macros(1, mc);
 
@@ -640,13 +603,13 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
             const int sm = (down ? k + 2 : k) & 3, s0 = (k + 1) & 3, sp = (down ? k : k + 2) & 3;
             const bool onS = !py && j == 0, onN = !py && j == ny - 1;
             const bool onW = !px && x == 0, onE = !px && x == nx - 1;
-            A grx, gry, gpx, gpy;
+            R grx, gry, gpx, gpy;
             if (!(onS || onN || onW || onE)) {
                 // grad = 3 sum_i w_i e_i phi(x + e_i), w = 1/9 (axis), 1/36 (diagonal)
-                const A t = A(1.0 / 3.0), d = A(1.0 / 12.0);
-                const RhoP<A> ml = s_rp[sm][c - 1], mc_ = s_rp[sm][c], mr = s_rp[sm][c + 1];
-                const RhoP<A> zl = s_rp[s0][c - 1], zr = s_rp[s0][c + 1];
-                const RhoP<A> pl = s_rp[sp][c - 1], pc = s_rp[sp][c], pr = s_rp[sp][c + 1];
+                const R t = R(1.0 / 3.0), d = R(1.0 / 12.0);
+                const RhoP<R> ml = s_rp[sm][c - 1], mc_ = s_rp[sm][c], mr = s_rp[sm][c + 1];
+                const RhoP<R> zl = s_rp[s0][c - 1], zr = s_rp[s0][c + 1];
+                const RhoP<R> pl = s_rp[sp][c - 1], pc = s_rp[sp][c], pr = s_rp[sp][c + 1];
                 grx = t * (zr.r - zl.r) + d * ((pr.r - pl.r) + (mr.r - ml.r));
                 gry = t * (pc.r - mc_.r) + d * ((pr.r - mr.r) + (pl.r - ml.r));
                 gpx = t * (zr.p - zl.p) + d * ((pr.p - pl.p) + (mr.p - ml.p));
@@ -654,37 +617,37 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
             } else {
                 // wall node: one-sided second order along the inward normal,
                 // central along the wall
-                const A r0 = s_rp[s0][c].r, p0 = s_rp[s0][c].p;
+                const R r0 = s_rp[s0][c].r, p0 = s_rp[s0][c].p;
                 if (onW || onE) {
                     const int dx = onW ? 1 : -1;
-                    A r2, p2;
+                    R r2, p2;
                     rho_p_at<MC>(P, src, plane, pitch, x + 2 * dx, j, r2, p2);
-                    const A r1 = s_rp[s0][c + dx].r, p1 = s_rp[s0][c + dx].p;
-                    grx = A(dx) * (A(-3) * r0 + A(4) * r1 - r2) * A(0.5);
-                    gpx = A(dx) * (A(-3) * p0 + A(4) * p1 - p2) * A(0.5);
+                    const R r1 = s_rp[s0][c + dx].r, p1 = s_rp[s0][c + dx].p;
+                    grx = R(dx) * (R(-3) * r0 + R(4) * r1 - r2) * R(0.5);
+                    gpx = R(dx) * (R(-3) * p0 + R(4) * p1 - p2) * R(0.5);
                 } else {
-                    grx = (s_rp[s0][c + 1].r - s_rp[s0][c - 1].r) * A(0.5);
-                    gpx = (s_rp[s0][c + 1].p - s_rp[s0][c - 1].p) * A(0.5);
+                    grx = (s_rp[s0][c + 1].r - s_rp[s0][c - 1].r) * R(0.5);
+                    gpx = (s_rp[s0][c + 1].p - s_rp[s0][c - 1].p) * R(0.5);
                 }
                 if (onS || onN) {
                     const int dy = onS ? 1 : -1;
-                    A r2, p2;
+                    R r2, p2;
                     rho_p_at<MC>(P, src, plane, pitch, x, j + 2 * dy, r2, p2);
-                    const A r1 = onS ? s_rp[sp][c].r : s_rp[sm][c].r;
-                    const A p1 = onS ? s_rp[sp][c].p : s_rp[sm][c].p;
-                    gry = A(dy) * (A(-3) * r0 + A(4) * r1 - r2) * A(0.5);
-                    gpy = A(dy) * (A(-3) * p0 + A(4) * p1 - p2) * A(0.5);
+                    const R r1 = onS ? s_rp[sp][c].r : s_rp[sm][c].r;
+                    const R p1 = onS ? s_rp[sp][c].p : s_rp[sm][c].p;
+                    gry = R(dy) * (R(-3) * r0 + R(4) * r1 - r2) * R(0.5);
+                    gpy = R(dy) * (R(-3) * p0 + R(4) * p1 - p2) * R(0.5);
                 } else {
-                    gry = (s_rp[sp][c].r - s_rp[sm][c].r) * A(0.5);
-                    gpy = (s_rp[sp][c].p - s_rp[sm][c].p) * A(0.5);
+                    gry = (s_rp[sp][c].r - s_rp[sm][c].r) * R(0.5);
+                    gpy = (s_rp[sp][c].p - s_rp[sm][c].p) * R(0.5);
                 }
             }
 
-            A v[18];
+            R v[18];
             const R* st = stage + (size_t)((k + 1) % S) * SST + E + tid;
 #pragma unroll
-            for (int q = 0; q < 18; ++q) v[q] = from_storage<A>(st[q * W]);
-            Mac<A> mf;
+            for (int q = 0; q < 18; ++q) v[q] = st[q * W];
+            Mac<R> mf;
             if (KEEP) {
                 lbm::expand<MC>(P, mc, mf);
             } else {
@@ -696,14 +659,7 @@ __global__ void __launch_bounds__(BX, KEEP ? FusedTraits<R, BX>::MINB : FusedTra
             // (no spills at 128 registers; re-reading them cost 0.6%)
             lbm::collide<MC>(P, mf, v, v + 9, grx, gry, gpx, gpy, add);
 
-            if constexpr (std::is_same<A, R>::value) {
-                push_node(dst, v, x, j, nx, ny, pitch, plane, px, py);
-            } else {
-                R w[18];
-#pragma unroll
-                for (int q = 0; q < 18; ++q) w[q] = to_storage<R>(v[q]);
-                push_node(dst, w, x, j, nx, ny, pitch, plane, px, py);
-            }
+            push_node(dst, v, x, j, nx, ny, pitch, plane, px, py);
         }
         if (KEEP) mc = mn;
     }
@@ -1665,11 +1621,27 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? LBM_BOUNDARY_MINB : 2) k
     wall_node(D, k, n);
 
     // the wall node's and x_f's populations, loaded together so that their
-    // latencies overlap (the pass is bound by them)
+    // latencies overlap (the pass is bound by them).  On a walled x side away
+    // from the corners the two nodes are neighbours in one row: when the
+    // pair starts on an even column it comes as one 8-byte (FP32) or
+    // 16-byte (FP64) load per population, which halves the load
+    // instructions and the DRAM sectors touched of a column of wall nodes.
     R v[18], u[18];
     const long long ib = (long long)n.y * pitch + n.x;
-    load18<R>(buf, plane, ib, v);
-    load18<R>(buf, plane, (long long)(n.y + n.dy) * pitch + (n.x + n.dx), u);
+    const int xl = n.dx > 0 ? n.x : n.x - 1;
+    if (n.dy == 0 && n.dx != 0 && (xl & 1) == 0) {
+        using V2 = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
+        const R* row = buf + (long long)n.y * pitch + xl;
+#pragma unroll
+        for (int q = 0; q < 18; ++q) {
+            const V2 pr = __ldg(reinterpret_cast<const V2*>(row + q * plane));
+            v[q] = n.dx > 0 ? pr.x : pr.y;
+            u[q] = n.dx > 0 ? pr.y : pr.x;
+        }
+    } else {
+        load18<R>(buf, plane, ib, v);
+        load18<R>(buf, plane, (long long)(n.y + n.dy) * pitch + (n.x + n.dx), u);
+    }
     // density (and Neumann total energy) from the bounced-back populations
     R rd, jx, jy, sg;
     lbm::node_sums(v, v + 9, rd, jx, jy, sg);
@@ -2218,10 +2190,9 @@ struct lbm_ctx {
 // one node per thread recomputing the macros, fewer registers (indices 9-11,
 // pair = 3); one autonomous warp per 30 columns, 1, 2 or 4 warps per CTA
 // (indices 12-14, pair = 4); one autonomous warp per 60 columns, two nodes
-// per lane in packed FP32 (indices 15-17, pair = 5); block strips of 32 or
-// 128 columns with FP64 storage and double-float arithmetic (indices 18-19,
-// pair = 6).  Variants 3-11 and 15-17 need FP32 storage, 18-19 FP64.
-constexpr int kVariants = 20;
+// per lane in packed FP32 (indices 15-17, pair = 5).  Variants 3-11 and
+// 15-17 need FP32 storage.
+constexpr int kVariants = 18;
 constexpr int kModels = 2;  // model classes: lbm::MODEL_ANY, lbm::MODEL_CAVITY
 // Lattices below this many nodes keep the generic instance even with the
 // cavity model: they are latency-bound, and batches of them (the serving
@@ -2435,14 +2406,14 @@ lbm_status upload_work(lbm_ctx* c) {
     return LBM_OK;
 }
 
-template <typename R, int BX, bool KEEP = true, int MC = lbm::MODEL_ANY, typename A = R>
+template <typename R, int BX, bool KEEP = true, int MC = lbm::MODEL_ANY>
 cudaError_t configure_collide() {
     constexpr int S = FusedTraits<R, BX>::S;
-    cudaError_t e = cudaFuncSetAttribute(k_collide_stream<R, BX, S, KEEP, MC, A>,
+    cudaError_t e = cudaFuncSetAttribute(k_collide_stream<R, BX, S, KEEP, MC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FusedSmem<R, BX, S>::bytes);
     if (e != cudaSuccess) return e;
     // prefer shared memory over L1: the row stages, not L1, feed the kernel
-    return cudaFuncSetAttribute(k_collide_stream<R, BX, S, KEEP, MC, A>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    return cudaFuncSetAttribute(k_collide_stream<R, BX, S, KEEP, MC>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                 (int)cudaSharedmemCarveoutMaxShared);
 }
 
@@ -2509,11 +2480,6 @@ lbm_status configure_kernels() {
     if (e == cudaSuccess) e = configure_collide<double, 32>();
     if (e == cudaSuccess) e = configure_collide<double, 64>();
     if (e == cudaSuccess) e = configure_collide<double, 128>();
-    // FP64 storage with double-float arithmetic, both model classes
-    if (e == cudaSuccess) e = configure_collide<double, 32, true, lbm::MODEL_ANY, ff64>();
-    if (e == cudaSuccess) e = configure_collide<double, 128, true, lbm::MODEL_ANY, ff64>();
-    if (e == cudaSuccess) e = configure_collide<double, 32, true, lbm::MODEL_CAVITY, ff64>();
-    if (e == cudaSuccess) e = configure_collide<double, 128, true, lbm::MODEL_CAVITY, ff64>();
     if (e == cudaSuccess) e = configure_warp<float, 1>();
     if (e == cudaSuccess) e = configure_warp<float, 2>();
     if (e == cudaSuccess) e = configure_warp<float, 4>();
@@ -2540,10 +2506,10 @@ int occupancy_of(K kernel, int threads, size_t smem) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess) n = 1;
     return std::max(n, 1);
 }
-template <typename R, int BX, bool KEEP, typename A = R>
+template <typename R, int BX, bool KEEP>
 int occ_collide() {
     constexpr int S = FusedTraits<R, BX>::S;
-    return occupancy_of(k_collide_stream<R, BX, S, KEEP, lbm::MODEL_ANY, A>, BX, FusedSmem<R, BX, S>::bytes);
+    return occupancy_of(k_collide_stream<R, BX, S, KEEP>, BX, FusedSmem<R, BX, S>::bytes);
 }
 template <int BX, bool KEEP>
 int occ_pair() { return occupancy_of(k_collide_pair<BX, KEEP>, BX / 2, PairSmem<BX>::bytes); }
@@ -2574,8 +2540,6 @@ int variant_per_sm(int vi, bool fp32) {
     case 15: return occ_warp2<1>();
     case 16: return occ_warp2<2>();
     case 17: return occ_warp2<4>();
-    case 18: return occ_collide<double, 32, true, ff64>();
-    case 19: return occ_collide<double, 128, true, ff64>();
     default: return fp32 ? occ_collide<float, 128, true>() : occ_collide<double, 128, true>();
     }
 }
@@ -2594,11 +2558,11 @@ long long resident_ctas(int vi, bool fp32) {
     return r;
 }
 
-template <typename R, int BX, bool KEEP = true, int MC = lbm::MODEL_ANY, typename A = R>
+template <typename R, int BX, bool KEEP = true, int MC = lbm::MODEL_ANY>
 void launch_collide_bx(const Work* work, int n, InstDesc* const* descs, int par, const long long* counter,
                        cudaStream_t s) {
     constexpr int S = FusedTraits<R, BX>::S;
-    k_collide_stream<R, BX, S, KEEP, MC, A><<<n, BX, FusedSmem<R, BX, S>::bytes, s>>>(work, descs, par, counter);
+    k_collide_stream<R, BX, S, KEEP, MC><<<n, BX, FusedSmem<R, BX, S>::bytes, s>>>(work, descs, par, counter);
 }
 
 template <typename R, int NW, int MC = lbm::MODEL_ANY>
@@ -2622,8 +2586,8 @@ void launch_pair_bx(const Work* work, int n, InstDesc* const* descs, int par, co
 }
 
 static const int kVariantWidth[kVariants] = {32, 64, 128, 64, 128, 256, 64, 128, 256, 32, 64, 128, 30, 60, 120,
-                                            60, 120, 240, 32, 128};
-static const int kVariantPair[kVariants] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 4, 4, 4, 5, 5, 5, 6, 6};
+                                            60, 120, 240};
+static const int kVariantPair[kVariants] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 4, 4, 4, 5, 5, 5};
 
 int variant_index(int bx, int pair) {
     for (int v = 0; v < kVariants; ++v)
@@ -2633,12 +2597,11 @@ int variant_index(int bx, int pair) {
 
 // Model class a launch of `variant` can use: the shapes that keep the row
 // macros (block strips, variants 0-2; paired block strips, variants 3-5;
-// warp strips, variants 12-14; double-float block strips, 18-19) have
-// instances specialised for the heated-cavity model (the one-node-per-thread
-// ones still give the same bits for a lattice); every other shape runs the
-// generic instance.
+// warp strips, variants 12-14) have instances specialised for the
+// heated-cavity model (the one-node-per-thread ones still give the same bits
+// for a lattice); every other shape runs the generic instance.
 int launch_model(int variant, int mc) {
-    return (variant <= 5 || (variant >= 12 && variant <= 14) || variant >= 18) ? mc : lbm::MODEL_ANY;
+    return (variant <= 5 || (variant >= 12 && variant <= 14)) ? mc : lbm::MODEL_ANY;
 }
 
 template <typename R, int MC>
@@ -2653,13 +2616,6 @@ void launch_model_variant(const Work* work, int n, int variant, InstDesc* const*
     case 5: launch_pair_bx<256, true, MC>(work, n, descs, par, counter, s); break;
     case 12: launch_warp_nw<R, 1, MC>(work, n, descs, par, counter, s); break;
     case 13: launch_warp_nw<R, 2, MC>(work, n, descs, par, counter, s); break;
-    case 18:
-    case 19:
-        if constexpr (std::is_same<R, double>::value) {
-            if (variant == 18) launch_collide_bx<double, 32, true, MC, ff64>(work, n, descs, par, counter, s);
-            else launch_collide_bx<double, 128, true, MC, ff64>(work, n, descs, par, counter, s);
-        }
-        break;
     default: launch_warp_nw<R, 4, MC>(work, n, descs, par, counter, s); break;
     }
 }
@@ -3101,14 +3057,11 @@ lbm_status lbm_set_tile(lbm_ctx* c, int bx, int by, int pair) {
         CUDA_TRY(cudaStreamSynchronize(c->stream));
         return LBM_OK;
     }
-    if (pair != 0 && pair != 4 && pair != 6 && c->cfg.precision != LBM_FP32_DEV)
+    if (pair != 0 && pair != 4 && c->cfg.precision != LBM_FP32_DEV)
         return fail(LBM_EINVAL, "pair 1-3 and 5 need FP32 storage");
-    if (pair == 6 && c->cfg.precision != LBM_FP64)
-        return fail(LBM_EINVAL, "pair 6 (double-float arithmetic) needs FP64 storage");
     if (variant_index(bx, pair) < 0)
         return fail(LBM_EINVAL, pair == 4   ? "warp strips (pair 4) are 30, 60 or 120 columns"
                                 : pair == 5 ? "paired warp strips (pair 5) are 60, 120 or 240 columns"
-                                : pair == 6 ? "double-float block strips (pair 6) are 32 or 128 columns"
                                 : (pair == 1 || pair == 2) ? "paired strips (pair 1 or 2) are 64, 128 or 256 columns"
                                                            : "bx must be 32, 64 or 128");
     if (by < 1) return fail(LBM_EINVAL, "by must be >= 1");

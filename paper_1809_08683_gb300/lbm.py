@@ -17,7 +17,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "csrc", "lbm_gb300.cu")
 _DEPS = [_SRC, os.path.join(_HERE, "csrc", "lbm_node.cuh"), os.path.join(_HERE, "csrc", "lbm_f2.cuh"),
-         os.path.join(os.path.dirname(_HERE), "include", "lbm.h")]
+         os.path.join(_HERE, "csrc", "lbm_ff.cuh"), os.path.join(os.path.dirname(_HERE), "include", "lbm.h")]
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "liblbm_gb300.so")
 NVCC_FLAGS = ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",

@@ -88,12 +88,6 @@ def _fp64(cfg):
     return c
 
 
-def finish_tile(cfg):
-    """Launch shape of an FP64 finish: block strips in double-float
-    arithmetic (pair 6), 32 columns for narrow lattices, 128 otherwise, with
-    the FP64 default run length."""
-    return (128 if int(cfg["nx"]) > 64 else 32, max(1, min(8, int(cfg["ny"]) // 128)), 6)
-
 
 class _Timer:
     """Device time between start() and stop() on the serving stream (CUDA
@@ -142,13 +136,13 @@ class Server:
     stops improving moves to FP64 (fp32_stalled); None keeps FP32 to the
     end.  starvation_s: a request that has waited this long stops later
     arrivals from overtaking it (None: never).  finish_tile_fn: launch shape
-    of the FP64 lattice an FP32 solve finishes in (default: double-float
-    block strips, finish_tile; None: the FP64 default)."""
+    of the FP64 lattice an FP32 solve finishes in (None: the FP64
+    default)."""
 
     def __init__(self, max_slots: int = 64, mem_fraction: float = 0.85, chunk: int = 1000,
                  graph_steps: int = 10, stream=None, tile_fn=None, keep_fields: bool = False,
                  fp32_stall: float | None = 1e-4, starvation_s: float | None = None,
-                 finish_tile_fn=finish_tile):
+                 finish_tile_fn=None):
         import torch
         self.torch = torch
         self.max_slots = max_slots
@@ -338,7 +332,7 @@ class Server:
 
 
 def solve_sequential(req: Request, chunk: int = 1000, keep_fields: bool = False, fp32_stall: float | None = 1e-4,
-                     finish_tile_fn=finish_tile):
+                     finish_tile_fn=None):
     """Plain per-request solve: the lattice alone, per-step launches, the
     same residual schedule (and the same move from FP32 to FP64 once FP32
     stalls).  The baseline the batched server is compared to."""

@@ -487,43 +487,3 @@ def test_couette_variable_viscosity_closed_form(lbm, precision, Pr, eos):
             # constant viscosity would give u = U0 xi, far from this result
             assert np.sqrt(((ux - xi) ** 2).sum() / (xi ** 2).sum()) > 5 * eu
 
-
-# FP64 storage with double-float arithmetic (pair 6): the node arithmetic in
-# pairs of FP32 numbers carrying about 48 significant bits (relative
-# rounding of a few units in 2^-48 = 3.6e-15 per operation, against 1.1e-16
-# in FP64).  Over the thousands of steps these tests run, the fields stay
-# within the FP64 path's 1e-10 of the oracle.
-TOLFF = 1e-10
-
-
-@pytest.mark.parametrize("tile", [(32, 5, 6), (128, 9, 6)])
-def test_double_float_cavity_matches_oracle(orc, lbm, tile):
-    cfg = W.cavity(N=67, Ra=2e3, eps=0.6)
-    cfg["walls"][1]["u"] = (0.02, 0.0)
-    o, g, err = pair(orc, lbm, cfg, 1500, tile=tile)
-    assert_close(err, TOLFF)
-    assert abs(g.nusselt(W.WALL_W) / o.nusselt(W.WALL_W) - 1) < 1e-9
-
-
-@pytest.mark.parametrize("eos,gamma", [((W.EOS_DECOUPLING, ()), 1.4), ((W.EOS_CS, ()), 1.1),
-                                       ((W.EOS_CUBIC, (0.05, 0.2)), 1.3)])
-def test_double_float_every_eos_periodic(orc, lbm, eos, gamma):
-    cfg = W.periodic_box(150, 37, visc_law=1, eos=eos, gamma=gamma, force=(2e-5, -1e-5))
-    _, _, err = pair(orc, lbm, cfg, 300, seed=71, df=1e-4, tile=(128, 7, 6))
-    assert_close(err, TOLFF)
-
-
-def test_double_float_couette_config1(orc, lbm):
-    cfg = W.couette(nx=4, ny=64)
-    o, g, err = pair(orc, lbm, cfg, 20000, tile=(32, 8, 6))
-    assert_close(err, TOLFF)
-    assert_close(dev_errors(g.macros(), o.macros()), 1e-8)
-
-
-def test_double_float_rejected_for_fp32_storage(lbm):
-    g = lbm.Lattice(W.periodic_box(16, 8, precision=1))
-    assert g.L.lbm_set_tile(g.h, 128, 4, 6) == lbm.LBM_EINVAL
-    g2 = lbm.Lattice(W.periodic_box(16, 8))
-    assert g2.L.lbm_set_tile(g2.h, 64, 4, 6) == lbm.LBM_EINVAL    # 32 or 128 columns
-    g.close()
-    g2.close()

@@ -149,25 +149,3 @@ def test_peak_rates_are_positive(lbm):
     r = lbm.peak_rates()
     assert all(np.isfinite(v) and v > 1e9 for v in r.values()), r
 
-
-def test_double_float_batch_member_equals_alone(lbm):
-    """An FP64 lattice in double-float block strips (pair 6) gets the same
-    bits alone and in a batch with native-FP64 and FP32 members."""
-    import torch
-    stream = torch.cuda.Stream()
-    cfgs = [W.cavity(N=200, Ra=1e4, eps=0.5), W.cavity(N=90, Ra=3e3, eps=0.4), W.poiseuille(nx=6, ny=40, precision=1)]
-    a = [lbm.Lattice(c, stream=stream) for c in cfgs]
-    b = [lbm.Lattice(c, stream=stream) for c in cfgs]
-    for lats in (a, b):
-        lats[0].set_tile(128, 6, 6)
-        lats[1].set_tile(32, 4, 6)
-    for lat in a:
-        lat.step(40)
-    batch = lbm.Batch(b, graph_steps=10)
-    batch.step(40)
-    stream.synchronize()
-    for x, y in zip(a, b):
-        fx, gx = x.get_state()
-        fy, gy = y.get_state()
-        assert np.array_equal(fx, fy) and np.array_equal(gx, gy)
-    batch.close()
