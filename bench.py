@@ -315,7 +315,7 @@ def serving_run(n, n_compare):
 
 
 def steady_cavity512(tol=1e-8):
-    """Config 3: the 512^2 heated cavity at Ra = 1e6, eps = 0.6, ideal gas,
+    """The 512^2 heated cavity at Ra = 1e6, eps = 0.6, ideal gas,
     Sutherland viscosity, run from rest to residual `tol` in FP32 deviation
     storage, finished in FP64 once FP32 stalls; its lone launch shape from
     the autotuner.  Nu_ave and p*_ave against Table 2."""
@@ -412,7 +412,7 @@ def fp64_path(n_side=2048, steps=10):
 
 
 def steady_sweep_subset(tol=1e-5, max_side=256):
-    """Config 4's members of side <= max_side served as one batch from rest
+    """The 96-cavity sweep's members of side <= max_side served as one batch from rest
     to residual `tol` (FP32, FP64 finish where FP32 stalls): p50/p99 of the
     per-member time to steady."""
     from paper_1809_08683_gb300 import serve

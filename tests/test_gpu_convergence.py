@@ -1,5 +1,4 @@
-"""Solves run to the residual targets of configs 3 and 5, through the
-serving loop: FP32 deviation storage until its stochastic-rounding noise
+"""Solves run to residual targets of 1e-8, through the serving loop: FP32 deviation storage until its stochastic-rounding noise
 floor stops the residual from falling, then FP64 storage from the same state
 (lbm_copy_state) down to the target.  The results are checked against the
 same problem solved in FP64 alone and against Table 2 of the paper."""
@@ -47,8 +46,8 @@ def test_fp32_then_fp64_matches_fp64_alone(mods, kind):
         assert abs(mixed.result["nusselt"] / alone.result["nusselt"] - 1) < 1e-5
 
 
-def test_config3_reaches_1e8_and_table2(mods):
-    """Config 3: the 512^2 cavity at Ra = 1e6, eps = 0.6 to r < 1e-8 (Table 2:
+def test_cavity512_ra1e6_reaches_1e8_and_table2(mods):
+    """The 512^2 cavity at Ra = 1e6, eps = 0.6 to r < 1e-8 (Table 2:
     Nu_ave 8.7406, p*_ave 0.91820; agreement within 0.5%)."""
     lbm, serve = mods
     cfg = W.cavity(N=512, Ra=1e6, eps=0.6, precision=1)

@@ -100,13 +100,13 @@ def test_corrections_off_fp64(orc, lbm):
     assert_close(err, TOL64)
 
 
-def test_couette_config1_fp64(orc, lbm):
+def test_couette_4x64_fp64(orc, lbm):
     # 4 x 64, lid 0.05, both walls at T = 1, ideal gas, Pr 0.71, tau 0.8, 20000 steps
     _, _, err = pair(orc, lbm, W.couette(nx=4, ny=64), 20000)
     assert_close(err, TOL64)
 
 
-def test_poiseuille_config2_fp64(orc, lbm):
+def test_poiseuille_4x128_cubic_fp64(orc, lbm):
     # 4 x 128, cubic EOS a = 0.05, b = 0.2, gamma 1.3, Pr 0.7, 50000 steps
     _, _, err = pair(orc, lbm, W.poiseuille(nx=4, ny=128), 50000)
     assert_close(err, TOL64)
@@ -149,7 +149,7 @@ def test_cavity_512_bench_shape_fp64(orc, lbm):
     assert_close(err, TOL64)
 
 
-def test_poiseuille_config2_fp32(orc, lbm):
+def test_poiseuille_4x128_cubic_fp32(orc, lbm):
     cfg = W.poiseuille(nx=4, ny=128, precision=1)
     o, g, err = pair(orc, lbm, cfg, 50000)
     assert_close(err, TOL32)
@@ -180,7 +180,7 @@ def test_paired_fp32_walls(orc, lbm, N, tile):
     assert abs(g.nusselt(W.WALL_W) / o.nusselt(W.WALL_W) - 1) < 5e-3
 
 
-def test_paired_fp32_poiseuille_config2(orc, lbm):
+def test_paired_fp32_poiseuille_4x128_cubic(orc, lbm):
     cfg = W.poiseuille(nx=4, ny=128, precision=1)
     o, g, err = pair(orc, lbm, cfg, 50000, tile=(64, 32, 2))
     assert_close(err, TOL32)
@@ -345,7 +345,7 @@ def test_lean_one_node_shape_matches_oracle(orc, lbm):
     assert_close(err, TOL32)
 
 
-def test_couette_config1_fp32(orc, lbm):
+def test_couette_4x64_fp32(orc, lbm):
     cfg = W.couette(nx=4, ny=64, precision=1)
     o, g, err = pair(orc, lbm, cfg, 20000)
     assert_close(err, TOL32)

@@ -73,7 +73,9 @@ def fake_library(trace):
 
         def diagnostics(self, snapshot=False):
             trace["diag_calls"] += 1
-            return [({}, -4) if l.unstable() else ({"residual": l.residual()}, 0) for l in self.lattices]
+            return [({}, -4) if l.unstable() else
+                    ({"residual": l.residual(), "mass": 1.0, "pstar": 1.0, "umax": 0.0, "Tmean": 1.0}, 0)
+                    for l in self.lattices]
 
         def close(self):
             pass
