@@ -240,6 +240,7 @@ class Server:
                 if not future:
                     # everything has arrived, nothing is resident, nothing fits
                     raise RuntimeError(f"request {pending[0].rid} does not fit the device budget")
+                t_diag = None   # waiting for arrivals is not host overhead
                 time.sleep(max(0.0, min(0.01, future[0].arrival - now)))
                 continue
             if dirty:
@@ -305,7 +306,7 @@ class Server:
         return requests
 
     def _switch_to_fp64(self, slot):
-        """Move a converged FP32 solve to FP64 storage (state, step count and
+        """Move a stalled FP32 solve to FP64 storage (state, step count and
         residual snapshot copied); False when the FP64 lattice does not fit
         now (the solve then stays in FP32 and retries after the next chunk)."""
         cfg = _fp64(slot.lat.cfg)
