@@ -72,6 +72,7 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="keep the built-in launch shapes")
     ap.add_argument("--serving", type=int, default=200,
                     help="requests in the served Poisson stream (0 to skip)")
+    ap.add_argument("--serving-sides", default="24,96", help="smallest,largest side of the served stream")
     ap.add_argument("--serving-compare", type=int, default=12,
                     help="requests of the stream also solved batched/one at a time x FP32/FP64")
     ap.add_argument("--no-steady", action="store_true", help="skip the time-to-steady runs")
@@ -253,12 +254,10 @@ def _field_errors(a, b):
             "T_dev": float(np.abs(a["T"] - b["T"]).max() / max(np.abs(b["T"] - 1.0).max(), 1e-300))}
 
 
-SERVING_SIDES = (24, 96)
-
-
-def serving_run(n, n_compare):
+def serving_run(n, n_compare, sides=(24, 96)):
     """Continuous batching of a seeded Poisson stream of n cavity and channel
-    solves (mean inter-arrival 50 ms, sides 24..96, FP32 deviation storage
+    solves (mean inter-arrival 50 ms, sides log-uniform in `sides` (24..96 by
+    default), FP32 deviation storage
     finished in FP64 where FP32 stalls, residual target 1e-7, cap 600,000
     steps), honouring arrival times.  The first n_compare requests are also
     solved three more ways for the attribution of the speed-up: batched in
@@ -266,7 +265,7 @@ def serving_run(n, n_compare):
     FP64 only (all with every request available at once); each FP32 result
     is compared with its own FP64 solve."""
     from paper_1809_08683_gb300 import serve
-    mix = W.serving_mix(n=n, seed=1810, min_side=SERVING_SIDES[0], max_side=SERVING_SIDES[1],
+    mix = W.serving_mix(n=n, seed=1810, min_side=sides[0], max_side=sides[1],
                         mean_interarrival=0.05, tol=1e-7, max_steps=600_000, precision=1)
     reqs = _requests(mix, 1)
     srv = serve.Server(max_slots=64, chunk=1000, graph_steps=10)
@@ -282,8 +281,8 @@ def serving_run(n, n_compare):
            "host_overhead": srv.host_overhead, "device_busy": srv.device_busy, "host_s": srv.host_s,
            "chunks": srv.chunks,
            "batch_rebuilds": srv.rebuilds,
-           "mix": f"Poisson stream (mean 50 ms), cavities and channels, sides {SERVING_SIDES[0]}.."
-                  f"{SERVING_SIDES[1]}, seed 1810, FP32 then FP64 where FP32 stalls"}
+           "mix": f"Poisson stream (mean 50 ms), cavities and channels, sides {sides[0]}..{sides[1]}, "
+                  f"seed 1810, FP32 then FP64 where FP32 stalls"}
     if n_compare <= 0:
         return out
     sub = mix[:n_compare]
@@ -629,7 +628,8 @@ def main():
         steady = {"cavity512": steady_cavity512(), "sweep_subset": steady_sweep_subset()}
     serving = None
     if rank == 0 and args.serving > 0:
-        serving = serving_run(args.serving, args.serving_compare)
+        serving = serving_run(args.serving, args.serving_compare,
+                              tuple(int(v) for v in args.serving_sides.split(",")))
 
     if rank == 0:
         desc = dict(desc)

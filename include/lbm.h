@@ -217,7 +217,9 @@ lbm_status lbm_set_tile(lbm_ctx* ctx, int bx, int by, int pair);
  * (FP32) or 8 (FP64); 3 ny / 512 between 1 and 12 for pair = 1.  by is
  * the run length when the lattice is stepped alone; a batch uses runs of
  * up to 24 (FP32; 32 for pair = 1) or 8 (FP64) rows for members whose
- * shape was not set, shortened until the batch fills the GPU. */
+ * shape was not set, shortened until the batch fills the GPU.  In either
+ * case the runs that make up the last fill of the GPU in a launch are cut
+ * into up to four runs of at least 6 rows, launched last. */
 lbm_status lbm_get_tile(const lbm_ctx* ctx, int* bx, int* by, int* pair);
 
 /* Steps taken since the last (re)initialisation. */
@@ -245,7 +247,9 @@ lbm_status lbm_batch_create(lbm_ctx* const* ctxs, int n, int graph_steps, lbm_ba
  * lbm_batch_create builds them; the batch handle stays valid and, if the
  * rebuild fails, unchanged.  Synchronises the batch stream.  LBM_EINVAL for
  * a context already in (add) or not in (remove) the batch, for one on
- * another stream, and for removing the last member. */
+ * another stream, and for removing the last member.  The paper has no
+ * counterpart: these serve requests that join and leave a running set of
+ * lattices. */
 lbm_status lbm_batch_add(lbm_batch* b, lbm_ctx* ctx);
 lbm_status lbm_batch_remove(lbm_batch* b, lbm_ctx* ctx);
 lbm_status lbm_batch_step(lbm_batch* b, long nsteps);
