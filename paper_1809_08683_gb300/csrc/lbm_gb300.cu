@@ -3354,23 +3354,40 @@ static void build_launch_set(lbm_ctx* const* ctxs, const std::vector<int>& membe
                              std::vector<Work>& all, std::vector<BWork>& ball) {
     std::vector<Work> groups[2][kVariants][kModels];
     std::vector<BWork> bgroups[2];
-    for (int i : members) {
+    // Members with longer runs first, and each member's runs together in
+    // make_work's order (row by row of runs, strips within a row): the
+    // CTAs that share a halo row or a 16-byte side chunk then run at about
+    // the same time and the second read of it comes from L2.  Sorting the
+    // runs themselves by length interleaved the members (their runs differ
+    // by a row) and left those re-reads to DRAM.
+    auto rows_of = [&](const lbm_ctx* c) {
+        return c->tile_set ? c->by : std::max(1, batch_rows(c->cfg, c->pair) >> shift);
+    };
+    auto run_len = [&](int i) {
+        const lbm_config& cf = ctxs[i]->cfg;
+        const long long nruns = (cf.ny + rows_of(ctxs[i]) - 1) / rows_of(ctxs[i]);
+        return (long long)((cf.ny + nruns - 1) / nruns);
+    };
+    std::vector<int> order(members);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return run_len(a) > run_len(b); });
+    for (int i : order) {
         const lbm_ctx* c = ctxs[i];
         const int pr = is_fp32(c) ? 1 : 0, bi = variant_index(c->bx, c->pair);
         const int par = (int)(c->steps & 1);
-        auto w = make_work(c->cfg, i, c->bx, c->tile_set ? c->by : std::max(1, batch_rows(c->cfg, c->pair) >> shift),
-                           par, c->steps);
+        auto w = make_work(c->cfg, i, c->bx, rows_of(c), par, c->steps);
         auto& grp = groups[pr][bi][launch_model(bi, c->mc)];
         grp.insert(grp.end(), w.begin(), w.end());
-        auto bw = make_bwork(c->cfg, i, par);
-        bgroups[pr].insert(bgroups[pr].end(), bw.begin(), bw.end());
     }
-    // longest runs first within each launch, and shorter runs at its end
+    for (int i : members) {
+        const lbm_ctx* c = ctxs[i];
+        auto bw = make_bwork(c->cfg, i, (int)(c->steps & 1));
+        bgroups[is_fp32(c) ? 1 : 0].insert(bgroups[is_fp32(c) ? 1 : 0].end(), bw.begin(), bw.end());
+    }
+    // shorter runs at the end of each launch
     for (int pr = 0; pr < 2; ++pr)
         for (int bi = 0; bi < kVariants; ++bi)
             for (int mc = 0; mc < kModels; ++mc) {
                 auto& g = groups[pr][bi][mc];
-                std::stable_sort(g.begin(), g.end(), [](const Work& a, const Work& b) { return a.y1 - a.y0 > b.y1 - b.y0; });
                 if (!g.empty()) split_tail(g, resident_ctas(bi, pr == 1));
                 ls.w_off[pr][bi][mc] = (int)all.size();
                 ls.w_cnt[pr][bi][mc] = (int)g.size();
