@@ -17,8 +17,9 @@ Fields of the JSON line (rank 0):
   ungraphed the same batch stepped with per-step launches and per-step
             CUDA events, which also give the fused/wall-pass split
   e2e       same metric through the public API with host buffers: per bench
-            step, equilibrium initialisation from pinned host fields (H2D),
-            the chunk of time steps, and the macroscopic fields back (D2H)
+            step, equilibrium initialisation of every cavity from pinned host
+            fields (H2D, lbm_batch_init_macros), the chunk of time steps, and
+            the macroscopic fields back (D2H, lbm_batch_macros)
   roofline  the fused kernel's algorithmic bytes (18 DF reads + 18 DF writes
             per node) over its CUDA-event duration, against the measured HBM
             copy bandwidth
@@ -589,15 +590,16 @@ def main():
                 t = torch.full(shp, v, dtype=torch.float64).pin_memory()
                 fields.append(t.numpy())
             host_in.append(fields)
-        host_out = [[torch.empty((c["ny"], c["nx"]), dtype=torch.float64).pin_memory().numpy()
-                     for _ in range(5)] for c in cfgs]
+        host_out = [{k: torch.empty((c["ny"], c["nx"]), dtype=torch.float64).pin_memory().numpy()
+                     for k in ("rho", "ux", "uy", "T", "p")} for c in cfgs]
 
         def e2e_step():
-            for lat, f in zip(lats, host_in):
-                lat.init_macros(*f)
+            # every member's fields up and results down, one round trip each way
+            batch.init_macros(host_in)
             batch.step(chunk)
-            for lat, o in zip(lats, host_out):
-                lat.check(lat.L.lbm_macros(lat.h, *(lbm._ptr(a) for a in o)))
+            st = batch.macros(host_out)
+            if any(v != lbm.LBM_OK for v in st):
+                raise lbm.LbmError(max(st, key=abs), "a member failed during the end-to-end run")
 
         e2e_step()  # untimed warm-up: the first host round trip of a process runs slow
         barrier()

@@ -274,6 +274,36 @@ lbm_status lbm_batch_step_profiled(lbm_batch* b, long nsteps, double* ms_collide
  * the residual checks of the serving loop. */
 lbm_status lbm_batch_diagnostics(lbm_batch* b, int snapshot, double* out8n, int* member_status);
 
+/* lbm_init_macros for every member of a batch, and lbm_macros for every
+ * member, each with one synchronisation of the batch stream: all host
+ * copies and kernels of all members are enqueued first, so the copies run
+ * back to back at the host link's rate instead of one stream round trip
+ * per member.  The fields are those of lbm_init_macros (Eq. decompose at
+ * the given rho, u, T with zero non-equilibrium part) and lbm_macros (Eqs.
+ * rho.u, E; T = eps / Cv; p = p_EOS).
+ *
+ * Arguments are arrays of n host pointers (n members, in the member order
+ * of lbm_batch_diagnostics: creation order, additions appended, removals
+ * closing the gap), each pointing to a caller-owned FP64 host array
+ * [ny][nx] (x fastest) of that member.  Pinned host memory gives the full
+ * copy rate; pageable memory works but serialises the copies.
+ *   lbm_batch_init_macros: rho, ux, uy, T must all be non-NULL and so must
+ *   every entry; each member's sticky status is cleared, as
+ *   lbm_init_macros clears it.  LBM_EINVAL before anything is enqueued
+ *   when an entry is NULL.
+ *   lbm_batch_macros: a NULL array skips that field for every member, a
+ *   NULL entry skips it for one member.  member_status (host, n entries,
+ *   may be NULL) receives each member's status as lbm_macros would return
+ *   it (LBM_OK, or a sticky LBM_EUNSTABLE / LBM_ETIMEOUT / LBM_ECUDA); the
+ *   call itself fails only on bad arguments or a failed CUDA call.  The
+ *   first call allocates one status word per member on the device.
+ * The paper has no counterpart: these move many problems' inputs and
+ * results between host and device in one round trip. */
+lbm_status lbm_batch_init_macros(lbm_batch* b, const double* const* rho, const double* const* ux,
+                                 const double* const* uy, const double* const* T);
+lbm_status lbm_batch_macros(lbm_batch* b, double* const* rho, double* const* ux, double* const* uy,
+                            double* const* T, double* const* p, int* member_status);
+
 /* Conserved sums of a context's current state, computed without allocating
  * anything.  The paper has no counterpart: this entry point is for callers
  * that may not allocate device memory, for example a host program that

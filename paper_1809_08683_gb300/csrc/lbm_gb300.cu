@@ -2224,6 +2224,7 @@ struct lbm_batch {
     DiagJob* d_jobs = nullptr;       // lbm_batch_diagnostics: one job per member, FP32 members first
     double* d_diag_out = nullptr;    // [member][kDiagSlots + 1] sums and status word
     std::vector<int> diag_order;     // members in job order
+    unsigned int* d_status_all = nullptr;  // lbm_batch_macros: every member's status word
 };
 
 namespace {
@@ -3620,12 +3621,80 @@ lbm_status lbm_batch_diagnostics(lbm_batch* b, int snapshot, double* out8n, int*
     return LBM_OK;
 }
 
+lbm_status lbm_batch_init_macros(lbm_batch* b, const double* const* rho, const double* const* ux,
+                                 const double* const* uy, const double* const* T) {
+    if (!b || !rho || !ux || !uy || !T) return fail(LBM_EINVAL, "bad batch init_macros arguments");
+    const int n = (int)b->ctxs.size();
+    for (int i = 0; i < n; ++i)
+        if (!rho[i] || !ux[i] || !uy[i] || !T[i]) return fail(LBM_EINVAL, "null field of batch member " + std::to_string(i));
+    // every member's copies and kernels on the shared stream, then one synchronisation
+    for (int i = 0; i < n; ++i) {
+        lbm_ctx* c = b->ctxs[i];
+        const long long nn = (long long)c->cfg.nx * c->cfg.ny;
+        const double* in[4] = {rho[i], ux[i], uy[i], T[i]};
+        for (int k = 0; k < 4; ++k)
+            CUDA_TRY(cudaMemcpyAsync(c->d_stage + k * nn, in[k], nn * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+        if (is_fp32(c))
+            k_init_macros<float><<<grid_for(nn), 256, 0, b->stream>>>(c->d_desc, cur_buf(c), c->d_stage, c->d_stage + nn,
+                                                                     c->d_stage + 2 * nn, c->d_stage + 3 * nn);
+        else
+            k_init_macros<double><<<grid_for(nn), 256, 0, b->stream>>>(c->d_desc, cur_buf(c), c->d_stage, c->d_stage + nn,
+                                                                      c->d_stage + 2 * nn, c->d_stage + 3 * nn);
+        lbm_status st = check_launch();
+        if (st != LBM_OK) return st;
+        CUDA_TRY(cudaMemsetAsync(c->d_status, 0, 256, b->stream));
+    }
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    for (lbm_ctx* c : b->ctxs) {
+        c->sticky = LBM_OK;
+        c->have_snap = false;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_macros(lbm_batch* b, double* const* rho, double* const* ux, double* const* uy,
+                            double* const* T, double* const* p, int* member_status) {
+    if (!b) return fail(LBM_EINVAL, "null batch");
+    const int n = (int)b->ctxs.size();
+    double* const* fields[5] = {rho, ux, uy, T, p};
+    if (!b->d_status_all && cudaMalloc(&b->d_status_all, (size_t)n * sizeof(unsigned int)) != cudaSuccess)
+        return fail(LBM_ENOMEM, "cudaMalloc batch status words");
+    for (int i = 0; i < n; ++i) {
+        lbm_ctx* c = b->ctxs[i];
+        const long long nn = (long long)c->cfg.nx * c->cfg.ny;
+        double* host[5];
+        double* dev[5];
+        for (int k = 0; k < 5; ++k) {
+            host[k] = fields[k] ? fields[k][i] : nullptr;
+            dev[k] = host[k] ? c->d_stage + k * nn : nullptr;
+        }
+        if (is_fp32(c)) k_macros<float><<<grid_for(nn), 256, 0, b->stream>>>(c->d_desc, cur_buf(c), dev[0], dev[1], dev[2], dev[3], dev[4]);
+        else k_macros<double><<<grid_for(nn), 256, 0, b->stream>>>(c->d_desc, cur_buf(c), dev[0], dev[1], dev[2], dev[3], dev[4]);
+        lbm_status st = check_launch();
+        if (st != LBM_OK) return st;
+        for (int k = 0; k < 5; ++k)
+            if (host[k]) CUDA_TRY(cudaMemcpyAsync(host[k], dev[k], nn * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+        CUDA_TRY(cudaMemcpyAsync(b->d_status_all + i, c->d_status, sizeof(unsigned int), cudaMemcpyDeviceToDevice, b->stream));
+    }
+    std::vector<unsigned int> words(n);
+    CUDA_TRY(cudaMemcpyAsync(words.data(), b->d_status_all, (size_t)n * sizeof(unsigned int), cudaMemcpyDeviceToHost, b->stream));
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    for (int i = 0; i < n; ++i) {
+        lbm_ctx* c = b->ctxs[i];
+        lbm_status ms = status_bits(c, words[i]);
+        if (ms == LBM_OK) ms = c->sticky;
+        if (member_status) member_status[i] = ms;
+    }
+    return LBM_OK;
+}
+
 lbm_status lbm_batch_destroy(lbm_batch* b) {
     if (!b) return LBM_OK;
     if (b->stream) cudaStreamSynchronize(b->stream);
     else cudaDeviceSynchronize();
     if (b->d_jobs) cudaFree(b->d_jobs);
     if (b->d_diag_out) cudaFree(b->d_diag_out);
+    if (b->d_status_all) cudaFree(b->d_status_all);
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->d_counter) cudaFree(b->d_counter);
     if (b->d_descs) cudaFree(b->d_descs);

@@ -75,7 +75,7 @@ EXPORTS = ("lbm_workspace_bytes", "lbm_create", "lbm_set_eos", "lbm_step", "lbm_
            "lbm_last_error", "lbm_batch_create", "lbm_batch_step", "lbm_batch_step_profiled",
            "lbm_batch_destroy", "lbm_conserved_sums_static", "lbm_set_rounding", "lbm_copy_state",
            "lbm_wait_selftest", "lbm_batch_diagnostics", "lbm_batch_add", "lbm_batch_remove",
-           "lbm_peak_rates")
+           "lbm_peak_rates", "lbm_batch_init_macros", "lbm_batch_macros")
 
 
 def load(path: str | None = None):
@@ -121,6 +121,8 @@ def load(path: str | None = None):
         L.lbm_batch_add.argtypes = [vp, vp]
         L.lbm_peak_rates.argtypes = [vp, dp]
         L.lbm_batch_remove.argtypes = [vp, vp]
+        L.lbm_batch_init_macros.argtypes = [vp, P(dp), P(dp), P(dp), P(dp)]
+        L.lbm_batch_macros.argtypes = [vp, P(dp), P(dp), P(dp), P(dp), P(dp), P(C.c_int)]
         _lib = L
         return L
 
@@ -132,6 +134,15 @@ def _check(L, st):
 
 def _ptr(a):
     return None if a is None else a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _host_field(a, lat, writable=False):
+    """Check that a is an FP64 C-contiguous host array of the lattice's
+    shape (it is passed to the library by pointer, not copied)."""
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags.c_contiguous \
+            or a.shape != (lat.ny, lat.nx) or (writable and not a.flags.writeable):
+        raise ValueError(f"expected a C-contiguous float64 array of shape {(lat.ny, lat.nx)}")
+    return a
 
 
 def make_config(cfg: dict) -> Config:
@@ -347,6 +358,41 @@ class Batch:
         _check(self.L, self.L.lbm_batch_diagnostics(self.h, int(bool(snapshot)), _ptr(a), st))
         keys = ("mass", "energy", "pstar", "residual", "nonfinite", "umax", "Tmean", "steps")
         return [(dict(zip(keys, a[8 * k:8 * k + 8].tolist())), int(st[k])) for k in range(n)]
+
+    def init_macros(self, fields):
+        """lbm_init_macros of every member with one synchronisation:
+        ``fields[k]`` is (rho, ux, uy, T) of member k, FP64 C-contiguous
+        host arrays [ny][nx] (pinned memory copies fastest)."""
+        n = len(self.lattices)
+        arrs = [[_host_field(a, lat) for a in f] for f, lat in zip(fields, self.lattices)]
+        if len(arrs) != n or any(len(f) != 4 for f in arrs):
+            raise ValueError("one (rho, ux, uy, T) per member")
+        cols = [(C.POINTER(C.c_double) * n)(*[_ptr(arrs[k][q]) for k in range(n)]) for q in range(4)]
+        _check(self.L, self.L.lbm_batch_init_macros(self.h, *cols))
+
+    def macros(self, out):
+        """lbm_macros of every member with one synchronisation: ``out[k]``
+        maps 'rho', 'ux', 'uy', 'T', 'p' (any subset) of member k to FP64
+        C-contiguous host arrays [ny][nx] that receive the fields.  Returns
+        each member's status (LBM_OK or its sticky error)."""
+        n = len(self.lattices)
+        if len(out) != n:
+            raise ValueError("one output dict per member")
+        keys = ("rho", "ux", "uy", "T", "p")
+        for o, lat in zip(out, self.lattices):
+            for k, a in o.items():
+                if k not in keys:
+                    raise ValueError(f"unknown field {k}")
+                _host_field(a, lat, writable=True)
+        cols = []
+        for k in keys:
+            if any(k in o for o in out):
+                cols.append((C.POINTER(C.c_double) * n)(*[_ptr(o.get(k)) for o in out]))
+            else:
+                cols.append(None)
+        st = (C.c_int * n)()
+        _check(self.L, self.L.lbm_batch_macros(self.h, *cols, st))
+        return [int(v) for v in st]
 
     def close(self):
         if getattr(self, "h", None):

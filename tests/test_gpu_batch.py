@@ -149,3 +149,53 @@ def test_batch_add_remove_keep_bits(lbm):
         batch.remove(lat)
     assert batch.L.lbm_batch_remove(batch.h, mixed[3].h) == lbm.LBM_EINVAL     # the last member stays
     batch.close()
+
+
+def test_batch_host_transfers_equal_lone_calls(lbm):
+    """lbm_batch_init_macros and lbm_batch_macros give every member the
+    bits lbm_init_macros and lbm_macros give it alone, FP32 and FP64
+    members alike, pinned and pageable host arrays, with fields skipped
+    for all members (a NULL array) or for one member (a NULL entry)."""
+    import torch
+    stream = torch.cuda.Stream()
+    cfgs = _mix()
+    alone = [lbm.Lattice(c, stream=stream) for c in cfgs]
+    mixed = [lbm.Lattice(c, stream=stream) for c in cfgs]
+    batch = lbm.Batch(mixed, graph_steps=0)
+    fields = []
+    for k, c in enumerate(cfgs):
+        f = W.random_macros(c["nx"], c["ny"], seed=100 + k, drho=0.01, du=0.01, dT=0.02)
+        if k % 2:   # pinned copies for every other member
+            f = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in f]
+        fields.append([np.ascontiguousarray(a) for a in f])
+    for lat, f in zip(alone, fields):
+        lat.init_macros(*f)
+    batch.init_macros(fields)
+    for a, m in zip(alone, mixed):
+        fa, ga = a.get_state()
+        fm, gm = m.get_state()
+        assert np.array_equal(fa, fm) and np.array_equal(ga, gm)
+    batch.step(40)
+    for a in alone:
+        a.step(40)
+    stream.synchronize()
+    out = []
+    for k, c in enumerate(cfgs):
+        keys = ("rho", "ux", "uy", "T") if k == 2 else ("rho", "ux", "uy", "T", "p")
+        out.append({q: np.full((c["ny"], c["nx"]), np.nan) for q in keys})
+    assert batch.macros(out) == [lbm.LBM_OK] * len(cfgs)
+    for k, (a, o) in enumerate(zip(alone, out)):
+        ref = a.macros()
+        for q, v in o.items():
+            assert np.array_equal(v, ref[q]), (k, q)
+    only_T = [{"T": np.empty((c["ny"], c["nx"]))} for c in cfgs]
+    assert batch.macros(only_T) == [lbm.LBM_OK] * len(cfgs)
+    for a, o in zip(alone, only_T):
+        assert np.array_equal(o["T"], a.macros()["T"])
+    # a NULL entry of the required init fields is refused before any work
+    bad = [list(f) for f in fields]
+    n = len(cfgs)
+    cols = [(lbm.C.POINTER(lbm.C.c_double) * n)(*[lbm._ptr(bad[k][q]) for k in range(n)]) for q in range(4)]
+    cols[1][3] = None
+    assert batch.L.lbm_batch_init_macros(batch.h, *cols) == lbm.LBM_EINVAL
+    batch.close()
