@@ -19,7 +19,8 @@ Fields of the JSON line (rank 0):
   e2e       same metric through the public API with host buffers: per bench
             step, equilibrium initialisation of every cavity from pinned host
             fields (H2D, lbm_batch_init_macros), the chunk of time steps, and
-            the macroscopic fields back (D2H, lbm_batch_macros)
+            the macroscopic fields back (D2H, lbm_batch_macros); with the rate
+            of a plain pinned copy of the same bytes each way on this machine
   roofline  the fused kernel's algorithmic bytes (18 DF reads + 18 DF writes
             per node) over its CUDA-event duration, against the measured HBM
             copy bandwidth
@@ -81,6 +82,10 @@ def parse():
                     help="instead of the benchmark: run the Table 2 cavity at this Ra (1e3..1e8) on its Table 1 "
                          "grid and print time-averaged Nu and p* (--table2-steps, averaged over the last half)")
     ap.add_argument("--table2-steps", type=int, default=2_000_000)
+    ap.add_argument("--sweep-steady", type=int, default=None, metavar="SIDE",
+                    help="instead of the benchmark: serve the 96-cavity sweep's members of side <= SIDE as one "
+                         "batch from rest to residual --sweep-steady-tol and print p50/p99 time to steady")
+    ap.add_argument("--sweep-steady-tol", type=float, default=1e-5)
     return ap.parse_args()
 
 
@@ -438,6 +443,32 @@ def steady_sweep_subset(tol=1e-5, max_side=256):
             "mlups": sum(r.steps * r.nodes for r in reqs) / srv.wall / 1e6}
 
 
+def host_link(h2d_bytes, d2h_bytes, dev, stream):
+    """Rate of one plain pinned-host copy of the end-to-end step's byte
+    counts in each direction (GB/s, best of 3): the copy floor that the
+    end-to-end figure carries on this machine."""
+    import torch
+    hi = torch.empty(h2d_bytes // 8, dtype=torch.float64).pin_memory()
+    ho = torch.empty(d2h_bytes // 8, dtype=torch.float64).pin_memory()
+    d = torch.empty(max(hi.numel(), ho.numel()), dtype=torch.float64, device=dev)
+    out = {}
+    with torch.cuda.stream(stream):
+        for name, fn, nbytes in (("h2d", lambda: d[:hi.numel()].copy_(hi, non_blocking=True), h2d_bytes),
+                                 ("d2h", lambda: ho.copy_(d[:ho.numel()], non_blocking=True), d2h_bytes)):
+            best = None
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                e1.synchronize()
+                t = e0.elapsed_time(e1)
+                best = t if best is None else min(best, t)
+            out[name] = nbytes / (best * 1e-3) / 1e9
+    del hi, ho, d
+    return out
+
+
 def max_over_ranks(value, world, dist=None, device=None):
     """The largest of a per-rank float over all ranks (all_reduce MAX), the
     bench's rule for timed regions; `value` itself when world == 1."""
@@ -505,6 +536,10 @@ def main():
     if args.table2 is not None:
         if rank == 0:
             print(json.dumps(table2_run(args.table2, args.table2_steps)))
+        return 0
+    if args.sweep_steady is not None:
+        if rank == 0:
+            print(json.dumps(steady_sweep_subset(tol=args.sweep_steady_tol, max_side=args.sweep_steady)))
         return 0
 
     cfgs, desc, chunk = workload(args.workload, args.precision)
@@ -610,7 +645,8 @@ def main():
         el = time.perf_counter() - t0
         el = max_over_ranks(el, world, dist, dev)
         e2e = {"value": whole_job_mlups(nodes, chunk * args.e2e_steps, world, el * 1e3), "unit": "MLUPS",
-               "h2d_bytes_per_step": nodes * 4 * 8, "d2h_bytes_per_step": nodes * 5 * 8}
+               "h2d_bytes_per_step": nodes * 4 * 8, "d2h_bytes_per_step": nodes * 5 * 8,
+               "host_link_gbps": host_link(nodes * 4 * 8, nodes * 5 * 8, dev, stream)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
