@@ -74,8 +74,8 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="keep the built-in launch shapes")
     ap.add_argument("--serving", type=int, default=200,
                     help="requests in the served Poisson stream (0 to skip)")
-    ap.add_argument("--serving-sides", default="24,96", help="smallest,largest side of the served stream")
-    ap.add_argument("--serving-compare", type=int, default=12,
+    ap.add_argument("--serving-sides", default="64,128", help="smallest,largest side of the served stream")
+    ap.add_argument("--serving-compare", type=int, default=6,
                     help="requests of the stream also solved batched/one at a time x FP32/FP64")
     ap.add_argument("--no-steady", action="store_true", help="skip the time-to-steady runs")
     ap.add_argument("--table2", type=float, default=None,
