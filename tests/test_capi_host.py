@@ -74,3 +74,11 @@ def test_workspace_grows_with_lattice_and_precision(L):
     _, b = _status(L, W.cavity(N=64, precision=1))
     _, c = _status(L, W.cavity(N=128, precision=0))
     assert b < a < c
+
+
+def test_batch_calls_reject_a_null_batch(L):
+    # the argument checks of the batch-level calls run before any CUDA call
+    assert L.lbm_batch_init_macros(None, None, None, None, None) == lbm.LBM_EINVAL
+    assert L.lbm_batch_macros(None, None, None, None, None, None, None) == lbm.LBM_EINVAL
+    assert L.lbm_batch_diagnostics(None, 0, None, None) == lbm.LBM_EINVAL
+    assert L.lbm_last_error()
