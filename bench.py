@@ -86,6 +86,7 @@ def parse():
                     help="instead of the benchmark: serve the 96-cavity sweep's members of side <= SIDE as one "
                          "batch from rest to residual --sweep-steady-tol and print p50/p99 time to steady")
     ap.add_argument("--sweep-steady-tol", type=float, default=1e-5)
+    ap.add_argument("--sweep-steady-deadline", type=float, default=None, help="seconds after which it stops")
     return ap.parse_args()
 
 
@@ -425,22 +426,29 @@ def fp64_path(n_side=2048, steps=10):
     return out
 
 
-def steady_sweep_subset(tol=1e-5, max_side=256):
+def steady_sweep_subset(tol=1e-5, max_side=256, deadline_s=None):
     """The 96-cavity sweep's members of side <= max_side served as one batch from rest
     to residual `tol` (FP32, FP64 finish where FP32 stalls): p50/p99 of the
-    per-member time to steady."""
+    per-member time to steady.  deadline_s stops the run after that many
+    seconds; percentiles then cover the members that finished."""
     from paper_1809_08683_gb300 import serve
     cfgs = [c for c in W.batched_sweep(precision=1) if c["nx"] <= max_side]
     reqs = [serve.Request(rid=i, cfg=c, tol=tol, max_steps=1_000_000) for i, c in enumerate(cfgs)]
     srv = serve.Server(max_slots=len(reqs), chunk=1000, graph_steps=1000)
-    srv.run(reqs, realtime=False)
-    return {"workload": f"batched_sweep_96_cavities members of side <= {max_side}", "members": len(reqs),
-            "tol": tol, **{k + "_s": v for k, v in serve.percentiles([r.latency for r in reqs]).items()},
-            "wall_s": srv.wall, "converged": sum(r.status == "converged" for r in reqs),
-            "capped": sum(r.status == "capped" for r in reqs),
-            "unstable": sum(r.status == "unstable" for r in reqs),
-            "finished_in_fp64": sum(r.switched_at is not None for r in reqs),
-            "mlups": sum(r.steps * r.nodes for r in reqs) / srv.wall / 1e6}
+    srv.run(reqs, realtime=False, deadline_s=deadline_s)
+    out = {"workload": f"batched_sweep_96_cavities members of side <= {max_side}", "members": len(reqs),
+           "tol": tol, **{k + "_s": v for k, v in serve.percentiles([r.latency for r in reqs]).items()},
+           "wall_s": srv.wall, "converged": sum(r.status == "converged" for r in reqs),
+           "capped": sum(r.status == "capped" for r in reqs),
+           "unstable": sum(r.status == "unstable" for r in reqs),
+           "finished_in_fp64": sum(r.switched_at is not None for r in reqs),
+           "mlups": sum(r.steps * r.nodes for r in reqs) / srv.wall / 1e6}
+    if deadline_s is not None:
+        out["deadline_s"] = deadline_s
+        out["stopped"] = sum(r.status == "stopped" for r in reqs)
+        out["stopped_sides"] = sorted({r.cfg["nx"] for r in reqs if r.status == "stopped"})
+        out["stopped_in_fp64"] = sum(r.status == "stopped" and r.switched_at is not None for r in reqs)
+    return out
 
 
 def host_link(h2d_bytes, d2h_bytes, dev, stream):
@@ -539,7 +547,8 @@ def main():
         return 0
     if args.sweep_steady is not None:
         if rank == 0:
-            print(json.dumps(steady_sweep_subset(tol=args.sweep_steady_tol, max_side=args.sweep_steady)))
+            print(json.dumps(steady_sweep_subset(tol=args.sweep_steady_tol, max_side=args.sweep_steady,
+                                                 deadline_s=args.sweep_steady_deadline)))
         return 0
 
     cfgs, desc, chunk = workload(args.workload, args.precision)

@@ -86,6 +86,18 @@ def fp32_stalled(history, ceiling=1e-4, window=20, gain=0.8):
     return min(history[-window:]) > gain * min(history[-2 * window:-window])
 
 
+def stall_window(cfg, base=20, ref_nodes=512 * 512):
+    """Residual checks that fp32_stalled compares for this lattice: `base`
+    up to 512^2 nodes, in proportion to the node count above.  The slowest
+    modes of a heated cavity relax on a diffusive time that grows with its
+    area: the 512^2 cavity at Ra = 1e6 loses a decade of residual in about
+    70,000 FP32 steps, and if that time scales with the area a 1024^2 one
+    loses it in about 280,000, a fall of less than 20% per 20 checks that a
+    fixed window of 20 would take for the noise floor."""
+    nodes = int(cfg["nx"]) * int(cfg["ny"])
+    return max(base, int(round(base * nodes / ref_nodes)))
+
+
 def _fp64(cfg):
     c = dict(cfg)
     c["precision"] = lbm.FP64
@@ -200,10 +212,13 @@ class Server:
         return lat
 
     # -- the loop ----------------------------------------------------------
-    def run(self, requests, realtime: bool = True):
+    def run(self, requests, realtime: bool = True, deadline_s: float | None = None):
         """Serve the requests; arrival times are honoured against the wall
         clock when realtime is True, otherwise every request is available at
-        once.  Returns the list of requests with their results filled."""
+        once.  deadline_s: after this many seconds of wall time the run
+        stops between chunks; resident solves are closed with status
+        "stopped" and requests not yet admitted stay "pending".  Returns the
+        list of requests with their results filled."""
         torch = self.torch
         pending = sorted(requests, key=lambda r: r.arrival)
         resident: list[_Slot] = []
@@ -214,6 +229,16 @@ class Server:
         t_diag = None           # when the last chunk's diagnostics returned
         while pending or resident:
             now = time.perf_counter() - t0
+            if deadline_s is not None and now > deadline_s:
+                if batch is not None:
+                    batch.close()
+                    batch = None
+                for slot in resident:
+                    slot.req.status = "stopped"
+                    self.in_use -= slot.bytes
+                    slot.lat.close()
+                resident = []
+                break
             ta = time.perf_counter()
             # admission: first fit in arrival order
             i = 0
@@ -277,7 +302,8 @@ class Server:
                     if r.steps >= r.min_steps and res < r.tol:
                         r.converged = True
                         r.status = "converged"
-                    elif fp32 and fp32_stalled(r.history, self.fp32_stall) and self._switch_to_fp64(slot):
+                    elif (fp32 and fp32_stalled(r.history, self.fp32_stall, stall_window(r.cfg))
+                          and self._switch_to_fp64(slot)):
                         r.switched_at = r.steps
                         dirty = True
                     if r.status == "running" and r.steps >= r.max_steps:
@@ -358,7 +384,8 @@ def solve_sequential(req: Request, chunk: int = 1000, keep_fields: bool = False,
         if req.steps >= req.max_steps:
             req.status = "capped"
             break
-        if int(lat.cfg.get("precision", 0)) == lbm.FP32_DEV and fp32_stalled(req.history, fp32_stall):
+        if (int(lat.cfg.get("precision", 0)) == lbm.FP32_DEV
+                and fp32_stalled(req.history, fp32_stall, stall_window(req.cfg))):
             lat64 = lbm.Lattice(_fp64(lat.cfg))
             if finish_tile_fn is not None:
                 lat64.set_tile(*finish_tile_fn(lat64.cfg))

@@ -287,3 +287,33 @@ def test_stall_rule():
     slow = [10 ** (-3 - k / 100) for k in range(40)]           # a decade per 100 checks: 0.63 per 20
     assert not serve.fp32_stalled(slow)
     assert not serve.fp32_stalled([1e-5] * 40, None)
+
+
+def test_stall_window_grows_with_the_lattice():
+    assert serve.stall_window(W.cavity(N=128)) == 20
+    assert serve.stall_window(W.cavity(N=512)) == 20
+    assert serve.stall_window(W.cavity(N=1024)) == 80
+    # a decade per 280 checks, the 512^2 rate of a decade per 70 checks
+    # scaled by the area of a 1024^2 lattice: below the ceiling the fixed
+    # window took it for the floor, the scaled one does not
+    slow = [10 ** (-4.2 - k / 280) for k in range(200)]
+    assert serve.fp32_stalled(slow, window=20)
+    assert not serve.fp32_stalled(slow, window=serve.stall_window(W.cavity(N=1024)))
+    # a flat floor is still seen, after twice the longer window
+    assert not serve.fp32_stalled([1e-6] * 159, window=80)
+    assert serve.fp32_stalled([1e-6] * 160, window=80)
+
+
+def test_deadline_stops_resident_solves(server_factory):
+    make, trace = server_factory
+    # two solves that never reach the target and a third that waits for a slot
+    reqs = make_requests([(0.0, 100, 0.999, None, 10**9), (0.0, 100, 0.999, None, 10**9),
+                          (0.0, 100, 0.1, None, 10**9)])
+    trace["step_sleep"] = 0.01
+    srv = make(10_000, max_slots=2, mem_fraction=1.0, chunk=1000, graph_steps=0)
+    t0 = time.perf_counter()
+    srv.run(reqs, realtime=False, deadline_s=0.2)
+    assert time.perf_counter() - t0 < 5.0
+    assert [r.status for r in reqs] == ["stopped", "stopped", "pending"]
+    assert reqs[0].steps > 0 and reqs[2].steps == 0
+    assert srv.in_use == 0
