@@ -82,3 +82,21 @@ def test_batch_calls_reject_a_null_batch(L):
     assert L.lbm_batch_macros(None, None, None, None, None, None, None) == lbm.LBM_EINVAL
     assert L.lbm_batch_diagnostics(None, 0, None, None) == lbm.LBM_EINVAL
     assert L.lbm_last_error()
+
+
+def test_host_field_checks():
+    # the batch transfer calls pass host arrays by pointer: only C-contiguous
+    # float64 arrays of the lattice's shape are accepted
+    import numpy as np
+    import types
+    lat = types.SimpleNamespace(nx=5, ny=3)
+    a = np.zeros((3, 5))
+    assert lbm._host_field(a, lat) is a
+    for bad in (np.zeros((3, 5), dtype=np.float32), np.zeros((5, 3)), np.zeros((3, 10))[:, ::2], [[0.0] * 5] * 3):
+        with pytest.raises(ValueError):
+            lbm._host_field(bad, lat)
+    ro = np.zeros((3, 5))
+    ro.flags.writeable = False
+    lbm._host_field(ro, lat)
+    with pytest.raises(ValueError):
+        lbm._host_field(ro, lat, writable=True)
